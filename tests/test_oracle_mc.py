@@ -1,0 +1,288 @@
+"""Pins of the oracle's Monte Carlo moves (Sec. 2: conditional hybrid algorithm on Eq. 2).
+
+The hybrid chain must sample the conditional Gibbs measure exp(-H/T) of Eq. 2 with the measured
+spins frozen. These tests check it against: exact properties of the over-relaxation move, the
+planar-rotator reflection it reduces to at q = 1, brute-force quadrature of the Gibbs measure on
+tiny lattices, the closed-form T -> infinity energies, and the T -> 0 ground state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+TWO_PI = 2.0 * math.pi
+
+
+def _H(phi, Lx, Ly, q=0.5):
+    """Eq. 2 with J = 1, open boundaries, written independently of the oracle (vectorised over
+    leading axes): phi has shape (..., Ly, Lx)."""
+    h = -np.cos(q * (phi[..., :, :-1] - phi[..., :, 1:])).sum(axis=(-1, -2))
+    v = -np.cos(q * (phi[..., :-1, :] - phi[..., 1:, :])).sum(axis=(-1, -2))
+    return h + v
+
+
+# --- over-relaxation ---------------------------------------------------------------------------
+
+def test_overrelax_conserves_energy_and_is_involution(orc):
+    rng = np.random.default_rng(0)
+    q = 0.5
+    n_moved = 0
+    for _ in range(20000):
+        hx, hy = rng.normal(size=2) * 2.0
+        f = rng.random() * TWO_PI
+        g, _ = orc.overrelax(q, hx, hy, f)
+        e0 = -(hx * math.cos(q * f) + hy * math.sin(q * f))
+        e1 = -(hx * math.cos(q * g) + hy * math.sin(q * g))
+        assert abs(e1 - e0) <= 1e-12
+        assert 0.0 <= g <= TWO_PI
+        back, _ = orc.overrelax(q, hx, hy, g)
+        assert abs(back - f) <= 1e-12
+        n_moved += g != f
+    assert n_moved > 5000       # the reflection is admissible a good part of the time
+
+
+def test_overrelax_q1_is_planar_rotator_reflection(orc):
+    # Eq. 1 (q = 1): the textbook over-relaxation phi' = 2*theta - phi (mod 2*pi), theta = arg h
+    rng = np.random.default_rng(1)
+    for _ in range(5000):
+        hx, hy = rng.normal(size=2)
+        f = rng.random() * TWO_PI
+        g, _ = orc.overrelax(1.0, hx, hy, f)
+        ref = (2.0 * math.atan2(hy, hx) - f) % TWO_PI
+        d = abs(g - ref)
+        assert min(d, TWO_PI - d) < 1e-12
+
+
+def test_overrelax_preserves_uniform_measure(orc):
+    # a measure-preserving involution maps uniform angles to uniform angles
+    from scipy import stats
+
+    rng = np.random.default_rng(2)
+    hx, hy = 1.3, -0.7
+    f = rng.random(20000) * TWO_PI
+    g = np.array([orc.overrelax(0.5, hx, hy, v)[0] for v in f])
+    assert stats.kstest(g / TWO_PI, "uniform").pvalue > 1e-3
+
+
+def test_overrelax_zero_field_keeps_angle(orc):
+    assert orc.overrelax(0.5, 0.0, 0.0, 1.234)[0] == 1.234
+
+
+# --- frozen sites ------------------------------------------------------------------------------
+
+def test_frozen_sites_bit_exact(orc):
+    rng = np.random.default_rng(4)
+    Lx, Ly = 17, 13
+    mask = (rng.random((Ly, Lx)) < 0.4).astype(np.uint8)
+    phi = rng.random((Ly, Lx)) * TWO_PI
+    o = orc.Oracle(Lx, Ly, seed=11)
+    out, _, _ = o.run(phi, mask, 0.7, 0, 60)
+    m = mask.astype(bool)
+    assert np.array_equal(out[m].view(np.uint64), phi[m].view(np.uint64))
+    assert np.all(out[~m] != phi[~m])
+
+
+# --- brute-force Gibbs measure on tiny lattices -------------------------------------------------
+
+def _exact_moments(Lx, Ly, frozen, T, n=48):
+    """<e_b> and <phi_s> of the conditional Gibbs measure by tensor Gauss-Legendre quadrature
+    over the free angles on [0, 2*pi]^k. frozen: dict site -> angle, every other site free."""
+    free = [s for s in range(Lx * Ly) if s not in frozen]
+    k = len(free)
+    x, w = np.polynomial.legendre.leggauss(n)
+    x = (x + 1.0) * math.pi
+    w = w * math.pi
+    grids = np.meshgrid(*([x] * k), indexing="ij")
+    wts = np.ones_like(grids[0])
+    for g in np.meshgrid(*([w] * k), indexing="ij"):
+        wts = wts * g
+    phi = np.zeros(grids[0].shape + (Ly * Lx,))
+    for s, a in frozen.items():
+        phi[..., s] = a
+    for i, s in enumerate(free):
+        phi[..., s] = grids[i]
+    phi = phi.reshape(grids[0].shape + (Ly, Lx))
+    H = _H(phi, Lx, Ly)
+    nb = Lx * (Ly - 1) + Ly * (Lx - 1)
+    b = np.exp(-(H - H.min()) / T) * wts
+    Z = b.sum()
+    e = float((b * H).sum() / Z / nb)
+    means = {s: float((b * grids[i]).sum() / Z) for i, s in enumerate(free)}
+    return e, means
+
+
+def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000):
+    mask = np.zeros((Ly, Lx), np.uint8)
+    phi = np.zeros((Ly, Lx))
+    for s, a in frozen.items():
+        mask.flat[s] = 1
+        phi.flat[s] = a
+    es, ms = [], []
+    for c in range(chains):
+        o = orc.Oracle(Lx, Ly, seed=1000 + c)
+        p = o.init(phi, mask)
+        p, _, _ = o.run(p, mask, T, 0, equil)
+        p, acc, e = o.run(p, mask, T, equil, nsweeps, acc=np.zeros_like(p), energies=True)
+        es.append(e.mean())
+        ms.append(acc / nsweeps)
+    es = np.array(es)
+    ms = np.array(ms)
+    return es.mean(), es.std(ddof=1) / math.sqrt(chains), ms.mean(0), ms.std(0, ddof=1) / math.sqrt(chains)
+
+
+CASES = [
+    # (Lx, Ly, frozen {site: angle}, T)
+    (3, 3, {0: 0.3, 1: 2.0, 2: 4.0, 3: 5.5, 5: 1.0, 6: 3.0, 7: 6.0, 8: 0.1}, 0.4),   # one free site
+    (3, 3, {0: 0.3, 1: 2.0, 2: 4.0, 3: 5.5, 5: 1.0, 6: 3.0, 7: 6.0, 8: 0.1}, 3.0),
+    (2, 2, {0: 1.0, 3: 4.0}, 0.5),                                                   # two free
+    (2, 2, {0: 5.0}, 0.8),                                                           # three free
+    (3, 3, {0: 0.5, 2: 5.0, 4: 3.0, 6: 1.5, 8: 6.0, 1: 2.5}, 0.6),                   # three free
+]
+
+
+@pytest.mark.parametrize("Lx,Ly,frozen,T", CASES)
+def test_mc_matches_brute_force_gibbs(orc, Lx, Ly, frozen, T):
+    e_ex, m_ex = _exact_moments(Lx, Ly, frozen, T)
+    e_ex2, _ = _exact_moments(Lx, Ly, frozen, T, n=64 if len(frozen) < Lx * Ly - 1 else 128)
+    assert abs(e_ex - e_ex2) < 1e-9           # quadrature converged
+    e_mc, e_se, m_mc, m_se = _mc_moments(orc, Lx, Ly, frozen, T)
+    assert abs(e_mc - e_ex) < 4.5 * e_se + 1e-4, (e_mc, e_ex, e_se)
+    for s, v in m_ex.items():
+        y, x = divmod(s, Lx)
+        assert abs(m_mc[y, x] - v) < 4.5 * m_se[y, x] + 1e-3, (s, m_mc[y, x], v, m_se[y, x])
+
+
+# --- T -> infinity and T -> 0 limits ----------------------------------------------------------
+
+def test_high_temperature_closed_form(orc):
+    # At T -> inf every prediction angle is uniform on [0, 2*pi] and independent:
+    #   pred-pred bond  E cos((a-b)/2) = (E sin(a/2))^2 = (2/pi)^2,
+    #   pred-frozen bond with frozen angle a: (2/pi) sin(a/2), frozen-frozen bond: fixed.
+    rng = np.random.default_rng(7)
+    Lx, Ly = 10, 8
+    mask = (rng.random((Ly, Lx)) < 0.5).astype(np.uint8)
+    phi = np.where(mask == 1, rng.random((Ly, Lx)) * TWO_PI, 0.0)
+    s = 0.0
+    nb = 0
+    for y in range(Ly):
+        for x in range(Lx):
+            for yy, xx in ((y, x + 1), (y + 1, x)):
+                if yy >= Ly or xx >= Lx:
+                    continue
+                nb += 1
+                a, b = mask[y, x], mask[yy, xx]
+                if a and b:
+                    s += math.cos(0.5 * (phi[y, x] - phi[yy, xx]))
+                elif a:
+                    s += (2 / math.pi) * math.sin(0.5 * phi[y, x])
+                elif b:
+                    s += (2 / math.pi) * math.sin(0.5 * phi[yy, xx])
+                else:
+                    s += 4 / math.pi**2
+    e_inf = -s / nb
+    o = orc.Oracle(Lx, Ly, seed=3)
+    p = o.init(phi, mask)
+    _, _, e = o.run(p, mask, 1e8, 0, 40000, energies=True)
+    se = e.std() / math.sqrt(e.size)
+    assert abs(e.mean() - e_inf) < 4 * se, (e.mean(), e_inf, se)
+    # unconditional limit -4/pi^2
+    o2 = orc.Oracle(12, 12, seed=4)
+    m0 = np.zeros((12, 12), np.uint8)
+    p2 = o2.init(np.zeros((12, 12)), m0)
+    _, _, e2 = o2.run(p2, m0, 1e8, 0, 20000, energies=True)
+    assert abs(e2.mean() + 4 / math.pi**2) < 4 * e2.std() / math.sqrt(e2.size)
+
+
+def _anneal(orc, o, phi, mask, T_end, stages=40, per=400):
+    sweep = 0
+    for T in np.geomspace(1.0, T_end, stages):
+        phi, _, _ = o.run(phi, mask, float(T), sweep, per)
+        sweep += per
+    return phi, sweep
+
+
+def test_low_temperature_chain_is_linear_interpolation(orc):
+    # T -> 0: a 1 x n chain with frozen ends a, b minimises H with equal steps
+    Lx, Ly = 10, 1
+    a, b = 0.5, 5.0
+    mask = np.zeros((1, Lx), np.uint8)
+    mask[0, 0] = mask[0, -1] = 1
+    phi = np.zeros((1, Lx))
+    phi[0, 0], phi[0, -1] = a, b
+    o = orc.Oracle(Lx, Ly, seed=21)
+    phi = o.init(phi, mask)
+    T = 1e-4
+    phi, sweep = _anneal(orc, o, phi, mask, T)
+    _, acc, _ = o.run(phi, mask, T, sweep, 4000, acc=np.zeros_like(phi))
+    mean = acc[0] / 4000
+    lin = a + (b - a) * np.arange(Lx) / (Lx - 1)
+    assert np.max(np.abs(mean[1:-1] - lin[1:-1])) < 0.01, mean - lin
+
+
+def test_low_temperature_unconditional_energy(orc):
+    # T -> 0 without frozen sites: all angles align and e_b -> -1
+    o = orc.Oracle(8, 8, seed=5)
+    m0 = np.zeros((8, 8), np.uint8)
+    p = o.init(np.zeros((8, 8)), m0)
+    p, sweep = _anneal(orc, o, p, m0, 1e-4, stages=40, per=300)
+    _, _, e = o.run(p, m0, 1e-4, sweep, 200, energies=True)
+    assert e.mean() < -1.0 + 2e-3
+
+
+# --- temperature dependence and tuning ---------------------------------------------------------
+
+def test_bond_energy_increases_with_temperature(orc):
+    import mpr_inputs
+
+    pr = mpr_inputs.make_problem(24, 24, 0.5, field_seed=1, mask_seed=2)
+    o = orc.Oracle(24, 24, seed=8)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    es = []
+    sweep = 0
+    for T in (0.02, 0.1, 0.5, 2.5, 12.5):
+        phi, _, _ = o.run(phi, pr.mask, T, sweep, 300)
+        phi, _, e = o.run(phi, pr.mask, T, sweep + 300, 300, energies=True)
+        sweep += 600
+        es.append(e.mean())
+    assert all(b > a for a, b in zip(es, es[1:])), es
+
+
+def test_tuning_recovers_temperature(orc):
+    # Draw an equilibrium configuration of Eq. 2 at T0 with no frozen site, keep half of it as
+    # measured data, and tune: the equilibrium bond energy at the tuned T must match the sample's
+    # and T must come back close to T0.
+    T0 = 0.35
+    L = 64
+    o = orc.Oracle(L, L, seed=31)
+    m0 = np.zeros((L, L), np.uint8)
+    p = o.init(np.zeros((L, L)), m0)
+    p, sweep = _anneal(orc, o, p, m0, T0, stages=10, per=200)
+    p, _, _ = o.run(p, m0, T0, sweep, 1000)
+    import mpr_inputs
+
+    mask = mpr_inputs.removal_mask(L, L, 0.5, seed=9)
+    o2 = orc.Oracle(L, L, seed=77)
+    e_s, _ = o2.energy_sample(p, mask)
+    start = o2.init(np.where(mask == 1, p, 0.0), mask)
+    st, T, _, _, trace = o2.tune(start, mask, e_s, 0, n_eq=150, n_meas=50)
+    assert st == 0
+    assert abs(T / T0 - 1.0) < 0.25, (T, trace)
+    # monotone bracket: the probe energies straddle e_s around the returned T
+    Ts = np.array([t for t, _ in trace])
+    Es = np.array([e for _, e in trace])
+    assert np.all(Es[Ts < 0.5 * T] < e_s) and np.all(Es[Ts > 2.0 * T] > e_s)
+
+
+def test_tuning_edge_cases(orc):
+    # a sample energy below what T_lo reaches returns T_lo; above T_hi's returns "no convergence"
+    import mpr_inputs
+
+    pr = mpr_inputs.make_problem(16, 16, 0.5, field_seed=5, mask_seed=6)
+    o = orc.Oracle(16, 16, seed=2)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    st, T, _, sw, tr = o.tune(phi, pr.mask, -1.5, 0, n_eq=20, n_meas=10)
+    assert st == 0 and T == 1e-3 and len(tr) == 1 and sw == 30
+    st, T, _, sw, tr = o.tune(phi, pr.mask, 0.5, 0, n_eq=20, n_meas=10)
+    assert st == 4 and T == 10.0 and len(tr) == 2 and sw == 60

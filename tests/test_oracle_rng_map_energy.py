@@ -1,0 +1,194 @@
+"""Pins of the oracle's random numbers, mapping, energies and prediction.
+
+Each test checks the oracle against something other than itself: numpy's own Philox generator,
+closed-form energies of hand-built states, exact rational bond counts, or the inverse mapping.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mpr_inputs
+
+TWO_PI = 2.0 * math.pi
+
+
+# --- Philox (Salmon et al., SC'11) -------------------------------------------------------------
+
+def test_philox4x64_matches_numpy(orc):
+    # numpy.random.Philox is Philox-4x64-10; it advances its counter by one before each block.
+    # The oracle's Philox is one routine for both word widths, so this pins the round structure,
+    # the key schedule and the word permutation that the 4x32 variant also runs through.
+    rng = np.random.default_rng(1)
+    for _ in range(64):
+        ctr = rng.integers(0, 2**63, size=4, dtype=np.uint64)
+        key = rng.integers(0, 2**63, size=2, dtype=np.uint64)
+        bg = np.random.Philox(counter=ctr, key=key)
+        got = bg.random_raw(4)
+        nxt = ctr.copy()
+        nxt[0] = np.uint64((int(ctr[0]) + 1) % 2**64)
+        exp = orc.philox(64, 10, nxt, key)
+        assert np.array_equal(got, exp)
+
+
+def test_philox4x32_uniform_and_avalanche(orc):
+    from scipy import stats
+
+    key = [0x1234567, 0x89ABCDE]
+    n = 1 << 14
+    words = np.array([orc.philox(32, 10, [i, 7, 0, 3], key) for i in range(n)], dtype=np.uint64)
+    assert words.max() < 2**32
+    for w in range(4):
+        top = (words[:, w] >> 24).astype(np.int64)
+        counts = np.bincount(top, minlength=256)
+        chi2 = ((counts - n / 256) ** 2 / (n / 256)).sum()
+        assert stats.chi2.sf(chi2, 255) > 1e-4
+    # neighbouring counters are uncorrelated
+    u = words.astype(np.float64) / 2**32
+    for w in range(4):
+        r = np.corrcoef(u[:-1, w], u[1:, w])[0, 1]
+        assert abs(r) < 4.0 / math.sqrt(n)
+    # avalanche: flipping one counter bit flips about half of the 128 output bits
+    rng = np.random.default_rng(5)
+    flips = []
+    for _ in range(200):
+        c = [int(v) for v in rng.integers(0, 2**32, size=4)]
+        base = orc.philox(32, 10, c, key)
+        b = int(rng.integers(0, 128))
+        c2 = list(c)
+        c2[b // 32] ^= 1 << (b % 32)
+        out = orc.philox(32, 10, c2, key)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(base, out)))
+    assert abs(np.mean(flips) / 128 - 0.5) < 0.02
+
+
+def test_site_words_distinct_streams(orc):
+    o = orc.Oracle(9, 7, seed=42)
+    seen = set()
+    for sweep in (0, 1):
+        for tag in (0, 1):
+            for y in range(7):
+                for x in range(9):
+                    seen.add(o.site_words(x, y, sweep, tag))
+    assert len(seen) == 2 * 2 * 63
+    # the two same-colour sites that share one Philox call take different words
+    a = o.site_words(0, 0, 3)
+    b = o.site_words(2, 0, 3)
+    ctr = [0, 0, 3, 0]
+    out = orc.philox(32, 10, ctr, [42, 0])
+    assert a == (int(out[0]), int(out[1])) and b == (int(out[2]), int(out[3]))
+
+
+def test_uniform_resolution(orc):
+    o32 = orc.Oracle(4, 4, ubits=32)
+    o23 = orc.Oracle(4, 4, ubits=23)
+    for w in (0, 1, 511, 512, 2**31, 2**32 - 1):
+        u = o32.uniform(w)
+        assert u == w / 2**32 and 0.0 <= u < 1.0
+        v = o23.uniform(w)
+        assert v == (w >> 9) / 2**23 and 0.0 <= v < 1.0
+
+
+# --- mapping and prediction --------------------------------------------------------------------
+
+def test_mapping_endpoints_and_roundtrip(orc):
+    pr = mpr_inputs.make_problem(33, 21, 0.4, field_seed=3, mask_seed=4)
+    o = orc.Oracle(33, 21)
+    phi, zmin, zmax = o.map(pr.z, pr.mask)
+    meas = pr.mask.astype(bool)
+    assert zmin == pr.z[meas].min() and zmax == pr.z[meas].max()
+    assert phi[meas].min() == 0.0 and phi[meas].max() == TWO_PI
+    # order preserving and affine
+    zz = pr.z[meas]
+    pp = phi[meas]
+    assert np.allclose(pp, TWO_PI * (zz - zmin) / (zmax - zmin), rtol=0, atol=1e-13)
+    # prediction inverts the mapping when every sample equals the mapped value
+    ns = 7
+    acc = np.where(meas, 0.0, phi * ns)
+    # put the true mapped value of the hidden sites into acc to test the inverse on them too
+    hidden_phi = TWO_PI * (pr.z - zmin) / (zmax - zmin)
+    acc = np.where(meas, 0.0, hidden_phi * ns)
+    zhat = o.predict(acc, ns, pr.z, pr.mask, zmin, zmax)
+    assert np.array_equal(zhat[meas], pr.z[meas])
+    assert np.allclose(zhat, pr.z, rtol=0, atol=1e-12)
+
+
+def test_mapping_degenerate(orc):
+    o = orc.Oracle(3, 3)
+    z = np.full((3, 3), 5.0)
+    m = np.zeros((3, 3), np.uint8)
+    m[0, 0] = m[1, 1] = 1
+    with pytest.raises(ValueError):
+        o.map(z, m)                      # zmax == zmin
+    z[1, 1] = 6.0
+    m2 = np.zeros((3, 3), np.uint8)
+    m2[0, 0] = 1
+    with pytest.raises(ValueError):
+        o.map(z, m2)                     # a single measured site
+    phi, lo, hi = o.map(z, m)
+    assert (lo, hi) == (5.0, 6.0)
+
+
+def test_init_uniform_and_frozen_untouched(orc):
+    o = orc.Oracle(64, 64, seed=9)
+    mask = mpr_inputs.removal_mask(64, 64, 0.5, seed=1)
+    phi0 = np.where(mask == 1, 1.25, 0.0)
+    phi = o.init(phi0, mask)
+    assert np.array_equal(phi[mask == 1], phi0[mask == 1])
+    free = phi[mask == 0]
+    assert free.min() >= 0.0 and free.max() < TWO_PI
+    from scipy import stats
+
+    assert stats.kstest(free / TWO_PI, "uniform").pvalue > 1e-4
+
+
+# --- energies (Eq. 2, e = <H>/N) ---------------------------------------------------------------
+
+@pytest.mark.parametrize("Lx,Ly", [(2, 2), (5, 3), (8, 8), (1, 6), (7, 1)])
+def test_energy_closed_forms(orc, Lx, Ly):
+    o = orc.Oracle(Lx, Ly)
+    nb = Lx * (Ly - 1) + Ly * (Lx - 1)
+    assert o.energy_bond(np.full((Ly, Lx), 2.0)) == -1.0
+    # vertical stripes phi = pi*(x mod 2): horizontal bonds cos(pi/2) = 0, vertical bonds cos 0 = 1
+    x = np.arange(Lx)[None, :].repeat(Ly, 0)
+    e = o.energy_bond(math.pi * (x % 2))
+    assert abs(e - (-(Lx * (Ly - 1)) / nb)) < 1e-15
+    # checkerboard: every bond joins angles 0 and pi -> cos(pi/2) = 0
+    y = np.arange(Ly)[:, None].repeat(Lx, 1)
+    assert abs(o.energy_bond(math.pi * ((x + y) % 2))) < 1e-15
+    # angles 0 and 2*pi are the two ends of the segment: cos(q*2*pi) = -1 on every bond
+    assert abs(o.energy_bond(TWO_PI * ((x + y) % 2)) - 1.0) < 1e-15
+
+
+def test_sample_energy_counts_measured_pairs(orc):
+    rng = np.random.default_rng(3)
+    Lx, Ly = 11, 9
+    mask = (rng.random((Ly, Lx)) < 0.5).astype(np.uint8)
+    phi = rng.random((Ly, Lx)) * TWO_PI
+    o = orc.Oracle(Lx, Ly)
+    e, n = o.energy_sample(phi, mask)
+    pairs = int((mask[:, :-1] & mask[:, 1:]).sum() + (mask[:-1, :] & mask[1:, :]).sum())
+    assert n == pairs
+    # brute force over the pairs with numpy
+    s = 0.0
+    for yy in range(Ly):
+        for xx in range(Lx):
+            if not mask[yy, xx]:
+                continue
+            if xx + 1 < Lx and mask[yy, xx + 1]:
+                s += math.cos(0.5 * (phi[yy, xx] - phi[yy, xx + 1]))
+            if yy + 1 < Ly and mask[yy + 1, xx]:
+                s += math.cos(0.5 * (phi[yy, xx] - phi[yy + 1, xx]))
+    assert abs(e + s / pairs) < 1e-14
+    with pytest.raises(ValueError):
+        o.energy_sample(phi, np.eye(Ly, Lx, dtype=np.uint8))   # no adjacent measured pair
+
+
+def test_aae_rmse_independent_of_oracle():
+    # AAE of Sec. 3 (Eq. 4) on a hand example; the harness metric is plain numpy
+    z = np.array([1.0, 2.0, 3.0, 4.0])
+    zh = np.array([1.5, 2.0, 2.0, 4.0])
+    pred = np.array([True, True, True, False])
+    err = z[pred] - zh[pred]
+    assert np.mean(np.abs(err)) == 0.5
+    assert abs(math.sqrt(np.mean(err**2)) - math.sqrt(1.25 / 3)) < 1e-15
