@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Throughput of the MPR gap-filling hot path on GB300: site-updates/s.
+
+One step = one whole gap-filling job through the C ABI on a synthetic Gaussian field with the
+exponential covariance of the paper's Sec. 3 (m = 50, sigma = 10, kappa = 0.2) at L = 4096 with
+90 % of the sites removed: mapping + initial state, temperature tuning, 2000 equilibration and
+200 sampling sweeps, prediction. A site-update is one hybrid move (Metropolis + over-relaxation)
+of one prediction site; the library counts them exactly (tuning probes included).
+
+  value  : inputs resident in device memory (mpr_create_dev / mpr_predict_dev)
+  e2e    : host buffers (pinned) through mpr_create / mpr_predict, copies inside the timing
+  --impl reference : the FP64 CPU oracle on this host's cores, on a bounded sample of sweeps
+
+Runs as one process per GPU under torchrun for N > 1: independent problems per rank (no data
+exchange), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+MUFU_PER_CLK_PER_SM = 16          # sin/cos/ex2/rcp/rsqrt lanes per SM per clock
+STORE_BYTES = {"D": 8, "S": 4, "H": 2, "B": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--p", type=float, default=0.9)
+    ap.add_argument("--setup", default="HDS", help="precision X_S X_E X_F (Sec. 2), e.g. HDS, SDS")
+    ap.add_argument("--acc", default="f64", choices=["f64", "kahan"])
+    ap.add_argument("--equil", type=int, default=2000)
+    ap.add_argument("--samples", type=int, default=200)
+    ap.add_argument("--ddd-sweeps", type=int, default=10, help="FP64 sweeps timed for the speedup")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks only; nothing of the method crosses ranks)
+# ------------------------------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "power_w_max": max(pw) if pw else None, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# the measured arm
+# ------------------------------------------------------------------------------------------------
+
+def sweep_kernel_id() -> str:
+    """Hash of the sweep kernel's sources: ties stored ncu counters to the code they came from."""
+    h = hashlib.sha256()
+    for f in ("mpr_sweep.cu", "mpr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_08448_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel_id: str, workload: str):
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload)
+    if not e or e.get("kernel_id") != kernel_id:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    except (OSError, ValueError):
+        return 6800.0, 2070.0, "fallback"
+
+
+def run_mine(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    import mpr_inputs
+    import paper_1910_08448_gb300 as mpr
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    mpr.load()
+    L, p = args.L, args.p
+    pr = mpr_inputs.make_problem(L, L, p, field_seed=1 + dist.rank, mask_seed=101 + dist.rank,
+                                 device=dev)
+    zt = torch.from_numpy(pr.z).to(dev)
+    mt = torch.from_numpy(pr.mask).to(dev)
+    out = torch.empty_like(zt)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    seed = 7 + dist.rank
+
+    def step_device(profile=False):
+        h = mpr.mpr_create_dev(zt, mt)
+        try:
+            mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+            if profile:
+                mpr.mpr_set_profiling(h, True)
+            T, _ = mpr.mpr_tune_temperature(h)
+            mpr.mpr_run(h, args.equil, args.samples)
+            mpr.mpr_predict_dev(h, out)
+            info = mpr.mpr_get_info(h)
+        finally:
+            mpr.mpr_destroy(h)
+        return info
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    # ---- timed: K steps, inputs resident, L2 flushed between steps outside the events ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dist.local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            infos.append(step_device(profile=True))
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms_local = sum(a.elapsed_time(b) for a, b in ev)
+    ms = dist.max(ms_local)
+    updates_local = float(sum(i["site_updates"] for i in infos))
+    updates = dist.sum(updates_local)
+    value = updates / (ms / 1e3)
+    launches = int(sum(i["kernel_launches"] for i in infos))
+
+    # ---- dominant kernel: sweep half-pass, device time from CUDA events inside the steps ----
+    sweep_ms = sum(i["prof_sweep_ms"] for i in infos)
+    sweep_launches = sum(i["prof_sweep_launches"] for i in infos)
+    t_launch = (sweep_ms / 1e3) / max(sweep_launches, 1)
+    N = L * L
+    b = STORE_BYTES[args.setup[0]]
+    bytes_launch = (N / 2) * (b * (2 + p) + 1 / 8)
+    mufu_launch = (N / 2) * (2 + 6 * p)
+    hbm_gbs, sm_mhz_max, src = peaks()
+    mufu_peak = SM_COUNT * MUFU_PER_CLK_PER_SM * sm_mhz_max * 1e6          # ops/s
+    t_hbm = bytes_launch / (hbm_gbs * 1e9)
+    t_mufu = mufu_launch / mufu_peak
+    kid = sweep_kernel_id()
+    workload = f"L{L}_p{p}_{args.setup}"
+    traffic = stored_traffic(kid, workload)
+    if t_hbm >= t_mufu:
+        roof = {"bound": "hbm", "achieved": bytes_launch / t_launch / 1e9, "peak": hbm_gbs,
+                "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": mufu_launch / t_launch / 1e9,
+                "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"traffic": traffic, "peak_source": src, "kernel": "mpr::sweep_kernel",
+                 "launch_us": t_launch * 1e6, "algorithmic_bytes_per_launch": bytes_launch,
+                 "algorithmic_mufu_per_launch": mufu_launch, "kernel_id": kid,
+                 "hbm_frac": bytes_launch / t_launch / 1e9 / hbm_gbs,
+                 "mufu_frac": mufu_launch / t_launch / mufu_peak})
+
+    # ---- FP64 (DDD) GPU path on the same lattice: speedup of the sweep kernel ----
+    T_last = infos[-1]["T"]
+    ddd = None
+    if args.ddd_sweeps > 0:
+        h = mpr.mpr_create_dev(zt, mt)
+        try:
+            mpr.mpr_set_options(h, "DDD", seed=seed)
+            mpr.mpr_set_temperature(h, T_last)
+            mpr.mpr_set_profiling(h, True)
+            mpr.mpr_run(h, 2, 0)
+            i0 = mpr.mpr_get_info(h)
+            mpr.mpr_run(h, args.ddd_sweeps, 0)
+            i1 = mpr.mpr_get_info(h)
+        finally:
+            mpr.mpr_destroy(h)
+        ddd_s = (i1["prof_sweep_ms"] - i0["prof_sweep_ms"]) / 1e3
+        ddd_rate = (i1["site_updates"] - i0["site_updates"]) / ddd_s
+        fast_rate = infos[-1]["n_pred"] / (2 * t_launch)
+        ddd = {"fp64_sweep_site_updates_per_s": ddd_rate,
+               "sweep_site_updates_per_s": fast_rate, "speedup_vs_fp64_gpu": fast_rate / ddd_rate}
+
+    # ---- end to end through the host API: pinned inputs, H2D + D2H inside the timing ----
+    e2e = None
+    if not args.no_e2e:
+        zp = torch.from_numpy(pr.z).pin_memory()
+        mp = torch.from_numpy(pr.mask).pin_memory()
+        zhat_host = torch.empty_like(zp).pin_memory()
+        zn, mn, on = zp.numpy(), mp.numpy(), zhat_host.numpy()
+        import ctypes
+
+        lib = mpr.load()
+        e_ms, e_upd = 0.0, 0
+        dist.barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = mpr.mpr_create(zn, mn)
+            try:
+                mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+                mpr.mpr_tune_temperature(h)
+                mpr.mpr_run(h, args.equil, args.samples)
+                mpr._check(lib.mpr_predict(h, on.ctypes.data_as(ctypes.c_void_p)))
+                e_upd += mpr.mpr_get_info(h)["site_updates"]
+            finally:
+                mpr.mpr_destroy(h)
+            torch.cuda.synchronize()
+            e_ms += (time.perf_counter() - t0) * 1e3
+        e_ms = dist.max(e_ms)
+        e_upd = dist.sum(float(e_upd))
+        e2e = {"value": e_upd / (e_ms / 1e3), "unit": "site-updates/s",
+               "h2d_bytes_per_step": int(pr.z.nbytes + pr.mask.nbytes),
+               "d2h_bytes_per_step": int(pr.z.nbytes), "ms_per_step": e_ms / args.steps}
+
+    # ---- accuracy of this run against the truth (prediction sites) ----
+    zhat = out.cpu().numpy()
+    pred = pr.mask == 0
+    err = (zhat - pr.z)[pred]
+    acc_rep = {"mae": float(np.mean(np.abs(err))), "rmse": float(np.sqrt(np.mean(err ** 2))),
+               "T": T_last, "e_bond_mean": infos[-1]["e_bond_mean"],
+               "e_sample": infos[-1]["e_sample"]}
+
+    return {
+        "value": value, "ms": ms, "updates": updates, "launches": launches, "roof": roof,
+        "ddd": ddd, "e2e": e2e, "clocks": clk.summary(), "accuracy": acc_rep,
+        "wall_s": t_wall, "site_updates_per_step": updates_local / args.steps,
+        "sweeps_per_step": infos[-1]["sweep"], "n_pred": infos[-1]["n_pred"], "problem": pr,
+    }
+
+
+def oracle_sample(L, p, setup, seconds, seed=7, pr=None):
+    """The FP64 oracle, as it stands, on a bounded number of sweeps of the same workload."""
+    import mpr_inputs
+    import oracle
+
+    oracle.build()
+    if pr is None:
+        pr = mpr_inputs.make_problem(L, L, p, field_seed=1, mask_seed=101)
+    o = oracle.Oracle(L, L, seed=seed, ubits=32 if setup[2] == "D" else 23)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    n_pred = int((pr.mask == 0).sum())
+    t0 = time.perf_counter()
+    phi, _, _ = o.run(phi, pr.mask, 0.5, 0, 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(seconds / max(t1, 1e-9)) - 1)
+    t0 = time.perf_counter()
+    o.run(phi, pr.mask, 0.5, 1, n)
+    t = time.perf_counter() - t0
+    return {"value": n * n_pred / t, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} hybrid sweeps of the {L}x{L} p={p} lattice at T=0.5 "
+                      f"({n * n_pred} site-updates, {t:.1f} s, 1 thread)"}
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    metric = f"site-updates/s at L={args.L} p={args.p}"
+    workload = (f"MPR gap filling, {args.L}x{args.L} Gaussian field (exp. covariance, kappa=0.2), "
+                f"{int(args.p * 100)}% removed: tune + {args.equil} equil + {args.samples} samples")
+    config = {"workload": workload, "L": args.L, "p": args.p, "setup": args.setup,
+              "acc": args.acc, "equil": args.equil, "samples": args.samples,
+              "l2": "flushed between steps (512 MB write)"}
+
+    if args.impl == "reference":
+        if dist.rank == 0:
+            import torch  # noqa: F401  (same process layout as the measured arm)
+
+            import mpr_inputs
+
+            pr = mpr_inputs.make_problem(args.L, args.L, args.p, field_seed=1, mask_seed=101)
+            vals = []
+            for k in range(args.warmup + args.steps):
+                r = oracle_sample(args.L, args.p, args.setup, args.cpu_seconds / 2, pr=pr)
+                if k >= args.warmup:
+                    vals.append(r)
+            v = statistics.mean(r["value"] for r in vals)
+            line = {"metric": metric, "value": v, "unit": "site-updates/s", "n_gpus": args.gpus,
+                    "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                    "impl": "reference", "dtype": "f64", "data": "synthetic", "config": config,
+                    "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": 1,
+                                     "kind": "oracle", "sample": vals[-1]["sample"]},
+                    "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                            "d2h_bytes_per_step": 0},
+                    "vs_baseline": None}
+            print(json.dumps(line), flush=True)
+        dist.close()
+        return
+
+    res = run_mine(args, dist)
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        cpu = oracle_sample(args.L, args.p, args.setup, args.cpu_seconds, pr=res["problem"])
+    if dist.rank == 0:
+        line = {
+            "metric": metric, "value": res["value"], "unit": "site-updates/s",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if args.setup[2] == "D" else "f32",
+            "data": "synthetic", "config": config,
+            "roofline": res["roof"], "cpu_baseline": cpu, "e2e": res["e2e"],
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "fp64_gpu": res["ddd"], "accuracy": res["accuracy"],
+            "site_updates_per_step": res["site_updates_per_step"],
+            "sweeps_per_step": res["sweeps_per_step"], "wall_s_timed": res["wall_s"],
+        }
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * mpr.h -- C ABI of libmpr: GPU (sm_103a) gap filling of 2-D gridded data with the modified
+ * planar rotator (MPR) model (Lach, Borovsky, Zukovic, "Numerical Precision Effects on GPU
+ * Simulation of Massive Spatial Data, Based on the Modified Planar Rotator Model").
+ *
+ * The method (Sec. 2): measured values are mapped onto spin angles that stay frozen; the spins of
+ * the prediction sites evolve by conditional Monte Carlo with the hybrid algorithm (Metropolis +
+ * energy-conserving over-relaxation) under H = -J sum_<ij> cos[q(phi_i - phi_j)] (Eq. 2, J = 1,
+ * q = 1/2 by default); the reduced temperature is the only parameter and is inferred from the
+ * data; predictions are averages of equilibrium configurations mapped back to the data scale.
+ * Precision settings follow the paper's three axes (Sec. 2): spin storage X_S, energy X_E and
+ * functions X_F, plus 16-bit spin storage (the paper's stated future work, Sec. 3).
+ *
+ * Conventions
+ *   - Grids are Lx x Ly, row-major, site s = y*Lx + x. Boundaries are open.
+ *   - Every call returns an mpr_status; nothing aborts or throws across the ABI. Arguments are
+ *     validated before any device work. mpr_last_error() gives a message for the calling thread.
+ *   - A handle is used by one host thread at a time. All device work of a handle is ordered on
+ *     its stream (default: the legacy default stream; see mpr_set_stream).
+ *   - "host" pointers are ordinary CPU memory (pinned memory makes the copies faster); "dev"
+ *     pointers are device memory of the current CUDA device, e.g. from torch. The library copies
+ *     inputs; the caller keeps ownership of every pointer it passes.
+ *   - The library allocates the device memory of a handle with cudaMalloc at creation and frees
+ *     it in mpr_destroy.
+ */
+#ifndef MPR_H
+#define MPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpr_ctx* mpr_handle;
+
+typedef enum {
+    MPR_OK = 0,
+    MPR_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, option out of range, NaN data  */
+    MPR_ERR_DEGENERATE = 2,       /* fewer than 2 measured sites, or zmax == zmin           */
+    MPR_ERR_NO_PAIRS = 3,         /* no two measured sites are neighbours: e_s undefined    */
+    MPR_ERR_TUNE_NO_CONVERGE = 4, /* sample energy above the bracket's top, or probes out   */
+    MPR_ERR_CUDA = 5,             /* a CUDA runtime call failed                              */
+    MPR_ERR_OOM = 6,              /* device allocation failed                                */
+    MPR_ERR_DEVICE_TIMEOUT = 7,   /* a bounded device-side wait ran out (batched kernel)    */
+    MPR_ERR_STATE = 8             /* call out of order, e.g. predict before any sample       */
+} mpr_status;
+
+/* Spin storage X_S (Sec. 2: DP or SP spin variables; 16-bit storage is the future work of Sec. 3). */
+typedef enum { MPR_STORE_F64 = 0, MPR_STORE_F32 = 1, MPR_STORE_F16 = 2, MPR_STORE_BF16 = 3 } mpr_store;
+/* Energy X_E and function X_F precision (Sec. 2): D = FP64, S = FP32 (functions: hardware
+ * intrinsics __sinf/__cosf/__expf, as the paper uses for all SP function evaluations). */
+typedef enum { MPR_PREC_D = 0, MPR_PREC_S = 1 } mpr_prec;
+/* Running sums of the sampled angles: FP64, or FP32 with Kahan compensation. */
+typedef enum { MPR_ACC_F64 = 0, MPR_ACC_KAHAN_F32 = 1 } mpr_acc;
+
+typedef struct {
+    uint64_t seed;     /* Philox-4x32-10 key (Salmon et al., SC'11); counters are (site, sweep) */
+    double q;          /* exponent of Eq. 2, 0 < q <= 1; 0 selects the default 1/2              */
+    int store;         /* mpr_store  (X_S)                                                      */
+    int energy;        /* mpr_prec   (X_E): the energy reduction                                */
+    int func;          /* mpr_prec   (X_F): sin/cos/exp/atan2 and the update arithmetic         */
+    int acc;           /* mpr_acc: prediction accumulators                                      */
+} mpr_options;
+
+/* Temperature tuning (Sec. 2: the reduced temperature is inferred from the incomplete data):
+ * bisection in log T on [T_lo, T_hi] for the T whose equilibrium bond energy of the conditional
+ * lattice equals the sample's, e_b(T) = e_s. Each probe runs n_eq sweeps, then averages e_b over
+ * n_meas sweeps; it stops when |e_b - e_s| <= rel_tol*|e_s| or T_hi/T_lo < ratio_tol. */
+typedef struct {
+    int n_eq;          /* default 200 */
+    int n_meas;        /* default 50  */
+    double T_lo;       /* default 1e-3 */
+    double T_hi;       /* default 10   */
+    double rel_tol;    /* default 1e-3 */
+    double ratio_tol;  /* default 1.001 */
+    int max_probes;    /* default 30, at most 64 */
+} mpr_tuning;
+
+typedef struct {
+    int Lx, Ly;
+    int64_t n_sites, n_pred, n_bonds, n_sample_pairs;
+    double zmin, zmax;         /* range of the measured values                               */
+    double e_sample;           /* e_s: per-bond energy of the measured-measured bonds         */
+    double T;                  /* current temperature (tuned or set), 0 if none               */
+    uint32_t sweep;            /* index of the next sweep (Philox counter)                    */
+    int n_samples;             /* sampling sweeps accumulated so far                          */
+    int n_probes;              /* probes of the last tuning                                   */
+    double e_bond_mean;        /* mean e_b over the sampling sweeps of the last mpr_run       */
+    uint64_t site_updates;     /* prediction-site hybrid moves done since creation            */
+    size_t device_bytes;       /* device memory held by the handle                            */
+    uint64_t kernel_launches;  /* kernels launched by the handle since creation               */
+    double prof_sweep_ms;      /* with profiling on: device time of the pure sweep segments   */
+    uint64_t prof_sweep_launches; /* ... and the number of sweep-kernel launches they hold    */
+} mpr_info;
+
+/* mpr_create: copies the host grid (values: Lx*Ly doubles, ignored where mask == 0 and may be
+ * NaN there; mask: Lx*Ly bytes, nonzero = measured/frozen), maps the measured values onto angles
+ * phi = 2*pi*(z - zmin)/(zmax - zmin) (Sec. 2: the data are mapped onto spins), draws uniform
+ * initial angles for the prediction sites and computes the sample energy e_s. Default options:
+ * seed 0, q = 1/2, FP32 spins, FP64 energy, FP32 intrinsic functions, FP64 accumulators.
+ * Errors: INVALID_ARG (Lx or Ly < 2, N > 2^31 - 1, NULL pointer, NaN/inf at a measured site),
+ * DEGENERATE, NO_PAIRS, OOM, CUDA. *out is NULL on error. */
+mpr_status mpr_create(int Lx, int Ly, const double* values, const unsigned char* mask,
+                      mpr_handle* out);
+/* Same, from device buffers, with all work on `stream` (a cudaStream_t, NULL = legacy default),
+ * which becomes the handle's stream. */
+mpr_status mpr_create_dev(int Lx, int Ly, const double* values_dev, const unsigned char* mask_dev,
+                          void* stream, mpr_handle* out);
+void mpr_destroy(mpr_handle h);
+
+/* Replaces the options and restarts the chain: the spins are re-initialised, the sweep counter,
+ * the samples and the temperature are cleared. */
+mpr_status mpr_set_options(mpr_handle h, const mpr_options* opt);
+mpr_status mpr_get_options(mpr_handle h, mpr_options* opt);
+mpr_status mpr_set_stream(mpr_handle h, void* stream);
+mpr_status mpr_set_tuning(mpr_handle h, const mpr_tuning* t);
+
+/* Runs the tuning from the current state (the chain continues through the probes) and sets the
+ * handle's temperature. TUNE_NO_CONVERGE still sets T (to T_hi, or the last bracket midpoint). */
+mpr_status mpr_tune_temperature(mpr_handle h, double* T_out);
+mpr_status mpr_set_temperature(mpr_handle h, double T);   /* T > 0; bypasses the tuning */
+
+/* equil sweeps, then samples sweeps after each of which every prediction angle is added to its
+ * accumulator (Sec. 2: averaging over configurations in equilibrium). One hybrid sweep updates
+ * all red prediction sites, then all black ones; each update is a Metropolis move with a uniform
+ * proposal followed by one over-relaxation move. May be called repeatedly; the sweep counter
+ * and the accumulators carry over. STATE if no temperature is set. */
+mpr_status mpr_run(mpr_handle h, int equil, int samples);
+
+/* Prediction zhat = zmin + (zmax - zmin) * mean(phi) / (2*pi) at prediction sites, the measured
+ * value elsewhere; out holds Lx*Ly doubles, row-major. STATE if no sample was taken. */
+mpr_status mpr_predict(mpr_handle h, double* out);
+mpr_status mpr_predict_dev(mpr_handle h, double* out_dev);
+
+/* e_bond = -(1/N_b) sum_<ij> cos[q(phi_i - phi_j)] of the current state, N_b = Lx(Ly-1)+Ly(Lx-1)
+ * (Eq. 2; Sec. 2 defines the specific energy e = <H>/L^2 = e_bond*N_b/N), computed in FP64;
+ * e_sample = e_s. Either pointer may be NULL. */
+mpr_status mpr_energy(mpr_handle h, double* e_bond, double* e_sample);
+mpr_status mpr_get_info(mpr_handle h, mpr_info* info);
+/* on != 0: bracket every run of sweeps without energy or sample work (equilibration) with CUDA
+ * events on the handle's stream and accumulate their device time into prof_sweep_ms. */
+mpr_status mpr_set_profiling(mpr_handle h, int on);
+
+/* State access for checkpoints and tests: angles as Lx*Ly doubles, row-major, host memory.
+ * mpr_set_state writes the prediction sites only (rounded to the storage type), leaves the
+ * frozen sites as mapped, and sets the next sweep index. */
+mpr_status mpr_get_state(mpr_handle h, double* angles, uint32_t* sweep);
+mpr_status mpr_set_state(mpr_handle h, const double* angles, uint32_t sweep);
+
+/* Philox-4x32-10 (Salmon et al., SC'11) as used by the sweeps: n counters of 4 words each
+ * (ctr_dev, device, 4n uint32) under key (seed_lo, seed_hi) -> 4n words in out_dev. */
+mpr_status mpr_philox4x32_10_dev(const uint32_t* ctr_dev, uint32_t* out_dev, int n, uint64_t seed,
+                                 void* stream);
+
+const char* mpr_status_string(mpr_status s);
+const char* mpr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPR_H */

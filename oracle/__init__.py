@@ -87,6 +87,8 @@ def lib():
             L.mpro_overrelax.restype = d
             L.mpro_update_site.argtypes = [P(Cfg), vp, vp, i, i, d, u32, P(d), P(d)]
             L.mpro_update_site.restype = d
+            L.mpro_half_sweep.argtypes = [P(Cfg), vp, vp, d, u32, i, vp, vp]
+            L.mpro_half_sweep.restype = None
             L.mpro_sweep.argtypes = [P(Cfg), vp, vp, d, u32, vp, vp]
             L.mpro_sweep.restype = None
             L.mpro_energy_bond.argtypes = [P(Cfg), vp]
@@ -187,6 +189,16 @@ class Oracle:
             return phi, mm, om
         lib().mpro_sweep(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), T, sweep, None, None)
         return phi
+
+    def half_sweep(self, phi, mask, T, sweep, colour):
+        """One colour of a sweep; returns (state, met_margin, or_margin), margins +inf elsewhere."""
+        phi = _f64(phi).copy()
+        m = _u8(mask)
+        mm = np.full_like(phi, np.inf)
+        om = np.full_like(phi, np.inf)
+        lib().mpro_half_sweep(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), T, sweep, colour,
+                              _ptr(mm), _ptr(om))
+        return phi, mm, om
 
     def run(self, phi, mask, T, sweep0, nsweeps, acc=None, energies: bool = False):
         """In-place on copies: returns (phi, acc, energies)."""

@@ -221,28 +221,36 @@ double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* m
     return mpro_overrelax(q, hx, hy, f1, or_margin);
 }
 
+void mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                     uint32_t sweep, int colour, double* met_margin, double* or_margin)
+{
+    const int Lx = cfg->Lx, Ly = cfg->Ly;
+    /* A site reads only neighbours of the other colour, so the sites of one colour can be
+     * overwritten in place. */
+    for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) {
+            if (((x + y) & 1) != colour) continue;
+            int s = y * Lx + x;
+            if (mask[s]) continue;
+            double mm, om;
+            double f = mpro_update_site(cfg, phi, mask, x, y, T, sweep, &mm, &om);
+            phi[s] = f;
+            if (met_margin) met_margin[s] = mm;
+            if (or_margin) or_margin[s] = om;
+        }
+}
+
 void mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,
                 double* met_margin, double* or_margin)
 {
-    const int Lx = cfg->Lx, Ly = cfg->Ly;
+    const int N = cfg->Lx * cfg->Ly;
     if (met_margin)
-        for (int s = 0; s < Lx * Ly; ++s) met_margin[s] = INFINITY;
+        for (int s = 0; s < N; ++s) met_margin[s] = INFINITY;
     if (or_margin)
-        for (int s = 0; s < Lx * Ly; ++s) or_margin[s] = INFINITY;
-    /* Red sites first, then black. A site reads only neighbours of the other colour, so the
-     * sites of one colour can be overwritten in place. */
-    for (int c = 0; c < 2; ++c)
-        for (int y = 0; y < Ly; ++y)
-            for (int x = 0; x < Lx; ++x) {
-                if (((x + y) & 1) != c) continue;
-                int s = y * Lx + x;
-                if (mask[s]) continue;
-                double mm, om;
-                double f = mpro_update_site(cfg, phi, mask, x, y, T, sweep, &mm, &om);
-                phi[s] = f;
-                if (met_margin) met_margin[s] = mm;
-                if (or_margin) or_margin[s] = om;
-            }
+        for (int s = 0; s < N; ++s) or_margin[s] = INFINITY;
+    /* red sites first, then black */
+    mpro_half_sweep(cfg, phi, mask, T, sweep, 0, met_margin, or_margin);
+    mpro_half_sweep(cfg, phi, mask, T, sweep, 1, met_margin, or_margin);
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -63,6 +63,10 @@ double mpro_overrelax(double q, double hx, double hy, double f, double* or_margi
  * or_margin = distance of the reflected angle to the ends of its admissible interval. */
 double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* mask, int x, int y,
                         double T, uint32_t sweep, double* met_margin, double* or_margin);
+/* The prediction sites of one colour (0 red, 1 black); margins as for mpro_sweep, written only at
+ * the sites it updates. */
+void mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                     uint32_t sweep, int colour, double* met_margin, double* or_margin);
 /* One hybrid sweep: all red prediction sites, then all black ones. The margin arrays (N, may be
  * NULL) receive each updated site's margins; other entries are set to +inf. */
 void mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,

@@ -1,0 +1,665 @@
+// mpr_api.cu -- host driver and C ABI of libmpr (declared in include/mpr.h).
+//
+// The handle owns the device state of one gap-filling problem: the data z and mask, the two
+// colour half-lattices of spin angles in the storage precision, the frozen-site bits, the
+// prediction accumulators and the reduction partials. The host side only validates, sequences
+// kernels on the handle's stream and runs the temperature bisection (Sec. 2: the temperature is
+// the single parameter inferred from the data) on scalars read back from the device.
+#include "mpr.h"
+#include "mpr_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace mpr;
+
+namespace {
+
+thread_local std::string g_err;
+
+mpr_status fail(mpr_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mpr_status fail(mpr_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (e_ == cudaErrorMemoryAllocation)                                              \
+                return fail(MPR_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));            \
+            return fail(MPR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
+        }                                                                                     \
+    } while (0)
+
+#define CHECK(st)                                                                             \
+    do {                                                                                      \
+        mpr_status s_ = (st);                                                                 \
+        if (s_ != MPR_OK) return s_;                                                          \
+    } while (0)
+
+mpr_options default_options()
+{
+    mpr_options o;
+    o.seed = 0;
+    o.q = 0.5;
+    o.store = MPR_STORE_F32;
+    o.energy = MPR_PREC_D;
+    o.func = MPR_PREC_S;
+    o.acc = MPR_ACC_F64;
+    return o;
+}
+
+mpr_tuning default_tuning()
+{
+    mpr_tuning t;
+    t.n_eq = 200;
+    t.n_meas = 50;
+    t.T_lo = 1e-3;
+    t.T_hi = 10.0;
+    t.rel_tol = 1e-3;
+    t.ratio_tol = 1.001;
+    t.max_probes = 30;
+    return t;
+}
+
+}  // namespace
+
+struct mpr_ctx {
+    int device = 0;
+    Layout L{};
+    Precision prec{};
+    mpr_options opt{};
+    mpr_tuning tune{};
+    cudaStream_t stream = nullptr;
+    long long N = 0, Np = 0, Nb = 0, Nss = 0;
+    double zmin = 0, zmax = 0, e_s = 0, T = 0;
+    bool have_T = false;
+    uint32_t sweep = 0;
+    int nsamples = 0, n_probes = 0;
+    double e_bond_mean = NAN;
+    uint64_t site_updates = 0;
+    size_t bytes = 0;
+    uint64_t launches = 0;
+
+    // optional CUDA-event timing of pure sweep segments
+    bool prof = false, prof_pending = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double prof_ms = 0.0;
+    uint64_t prof_launches = 0, prof_pending_launches = 0;
+
+    // device memory
+    double* z = nullptr;                 // N, row-major
+    unsigned char* mask = nullptr;       // N, row-major
+    void* ang[2] = {nullptr, nullptr};   // colour half-lattices, Ly x pitch, storage type
+    uint32_t* mb[2] = {nullptr, nullptr};
+    double* acc[2] = {nullptr, nullptr};
+    float* acc_hi[2] = {nullptr, nullptr};
+    float* acc_lo[2] = {nullptr, nullptr};
+    void* part = nullptr;                // reduction partials
+    size_t part_bytes = 0;
+    double* scal = nullptr;              // 16 device scalars
+    double* eseries = nullptr;           // raw bond sums of measured sweeps
+    int eseries_cap = 0;
+    double* tmpN = nullptr;              // N doubles for state transfer / prediction
+    double* host = nullptr;              // pinned host staging (16 doubles)
+};
+
+namespace {
+
+template <typename T>
+mpr_status dalloc(mpr_ctx* h, T** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? MPR_ERR_OOM : MPR_ERR_CUDA,
+                    "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    *p = static_cast<T*>(q);
+    h->bytes += bytes;
+    return MPR_OK;
+}
+
+template <typename T>
+void dfree(mpr_ctx* h, T** p, size_t bytes)
+{
+    if (*p) {
+        cudaFree(*p);
+        h->bytes -= bytes ? bytes : 16;
+    }
+    *p = nullptr;
+}
+
+size_t ang_bytes(const mpr_ctx* h) { return (size_t)h->L.Ly * h->L.pitch * store_bytes(h->prec.store); }
+size_t mb_bytes(const mpr_ctx* h) { return (size_t)h->L.Ly * h->L.mpitch * 4; }
+size_t accd_bytes(const mpr_ctx* h) { return (size_t)h->L.Ly * h->L.pitch * 8; }
+size_t accf_bytes(const mpr_ctx* h) { return (size_t)h->L.Ly * h->L.pitch * 4; }
+
+void free_state(mpr_ctx* h)
+{
+    for (int c = 0; c < 2; ++c) {
+        dfree(h, &h->ang[c], ang_bytes(h));
+        dfree(h, &h->mb[c], mb_bytes(h));
+        dfree(h, &h->acc[c], accd_bytes(h));
+        dfree(h, &h->acc_hi[c], accf_bytes(h));
+        dfree(h, &h->acc_lo[c], accf_bytes(h));
+    }
+}
+
+void free_all(mpr_ctx* h)
+{
+    free_state(h);
+    dfree(h, &h->z, (size_t)h->N * 8);
+    dfree(h, &h->mask, (size_t)h->N);
+    dfree(h, &h->part, h->part_bytes);
+    dfree(h, &h->scal, 16 * 8);
+    dfree(h, &h->eseries, (size_t)h->eseries_cap * 8);
+    dfree(h, &h->tmpN, (size_t)h->N * 8);
+    if (h->host) cudaFreeHost(h->host);
+    h->host = nullptr;
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    h->ev0 = h->ev1 = nullptr;
+}
+
+mpr_status harvest_profile(mpr_ctx* h)
+{
+    if (!h->prof_pending) return MPR_OK;
+    CU(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->prof_ms += ms;
+    h->prof_launches += h->prof_pending_launches;
+    h->prof_pending = false;
+    return MPR_OK;
+}
+
+mpr_status sync(mpr_ctx* h)
+{
+    CU(cudaStreamSynchronize(h->stream));
+    return harvest_profile(h);
+}
+
+mpr_status validate_options(const mpr_options* o)
+{
+    if (!o) return fail(MPR_ERR_INVALID_ARG, "options pointer is NULL");
+    if (o->store < 0 || o->store > 3) return fail(MPR_ERR_INVALID_ARG, "store %d out of range", o->store);
+    if (o->energy < 0 || o->energy > 1) return fail(MPR_ERR_INVALID_ARG, "energy %d out of range", o->energy);
+    if (o->func < 0 || o->func > 1) return fail(MPR_ERR_INVALID_ARG, "func %d out of range", o->func);
+    if (o->acc < 0 || o->acc > 1) return fail(MPR_ERR_INVALID_ARG, "acc %d out of range", o->acc);
+    if (!(o->q >= 0.0 && o->q <= 1.0)) return fail(MPR_ERR_INVALID_ARG, "q = %g outside (0, 1]", o->q);
+    return MPR_OK;
+}
+
+// Allocates the precision-dependent state, maps the data, draws the initial angles and computes
+// e_s (which depends on q). Clears the chain: sweep counter, samples, temperature.
+mpr_status init_state(mpr_ctx* h)
+{
+    free_state(h);
+    const Precision& p = h->prec;
+    for (int c = 0; c < 2; ++c) {
+        CHECK(dalloc(h, &h->ang[c], ang_bytes(h)));
+        CHECK(dalloc(h, &h->mb[c], mb_bytes(h)));
+        if (p.acc == 0) {
+            CHECK(dalloc(h, &h->acc[c], accd_bytes(h)));
+            CU(cudaMemsetAsync(h->acc[c], 0, accd_bytes(h), h->stream));
+        } else {
+            CHECK(dalloc(h, &h->acc_hi[c], accf_bytes(h)));
+            CHECK(dalloc(h, &h->acc_lo[c], accf_bytes(h)));
+            CU(cudaMemsetAsync(h->acc_hi[c], 0, accf_bytes(h), h->stream));
+            CU(cudaMemsetAsync(h->acc_lo[c], 0, accf_bytes(h), h->stream));
+        }
+    }
+    CU(launch_init(h->L, p, h->z, h->mask, h->scal, h->ang[0], h->ang[1], h->mb[0], h->mb[1],
+                   h->opt.seed, 0u, h->stream));
+    h->launches += 3;   // init + sample energy (2)
+    const int nb = sample_energy_blocks(h->L);
+    double* psum = static_cast<double*>(h->part);
+    long long* pcnt = reinterpret_cast<long long*>(psum + nb);
+    CU(launch_sample_energy(h->L, h->z, h->mask, h->scal, h->opt.q, psum, pcnt, nb, h->scal + 4,
+                            h->stream));
+    CU(cudaMemcpyAsync(h->host, h->scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CHECK(sync(h));
+    h->e_s = h->host[0];
+    h->Nss = (long long)h->host[1];
+    h->sweep = 0;
+    h->nsamples = 0;
+    h->have_T = false;
+    h->T = 0.0;
+    h->n_probes = 0;
+    h->e_bond_mean = NAN;
+    if (h->Nss == 0) return fail(MPR_ERR_NO_PAIRS, "no two measured sites are nearest neighbours");
+    return MPR_OK;
+}
+
+mpr_status create_common(int Lx, int Ly, const double* values, const unsigned char* mask,
+                         bool on_device, cudaStream_t stream, mpr_handle* out)
+{
+    if (!out) return fail(MPR_ERR_INVALID_ARG, "out pointer is NULL");
+    *out = nullptr;
+    if (!values || !mask) return fail(MPR_ERR_INVALID_ARG, "values or mask is NULL");
+    if (Lx < 2 || Ly < 2) return fail(MPR_ERR_INVALID_ARG, "grid %d x %d: both sides must be >= 2", Lx, Ly);
+    if ((long long)Lx * Ly > 2147483647LL)
+        return fail(MPR_ERR_INVALID_ARG, "grid %d x %d exceeds 2^31 - 1 sites", Lx, Ly);
+    mpr_ctx* h = new (std::nothrow) mpr_ctx();
+    if (!h) return fail(MPR_ERR_OOM, "host allocation failed");
+    h->stream = stream;
+    h->opt = default_options();
+    h->tune = default_tuning();
+    h->prec = Precision{h->opt.store, h->opt.energy, h->opt.func, h->opt.acc};
+    h->L.Lx = Lx;
+    h->L.Ly = Ly;
+    h->L.Lxh = (Lx + 1) / 2;
+    h->L.pitch = (h->L.Lxh + 63) / 64 * 64;
+    h->L.mpitch = h->L.pitch / 32;
+    h->N = (long long)Lx * Ly;
+    h->Nb = (long long)Lx * (Ly - 1) + (long long)Ly * (Lx - 1);
+    auto bail = [&](mpr_status s) {
+        std::string keep = g_err;
+        free_all(h);
+        delete h;
+        g_err = keep;
+        return s;
+    };
+    mpr_status s;
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(MPR_ERR_CUDA, "no CUDA device"));
+    if (cudaMallocHost(&h->host, 16 * sizeof(double)) != cudaSuccess)
+        return bail(fail(MPR_ERR_OOM, "pinned host allocation failed"));
+    const int nmm = 256;
+    h->part_bytes = (size_t)sweep_blocks(h->L, h->prec);
+    {
+        size_t need = h->part_bytes * 8;
+        size_t a = (size_t)sample_energy_blocks(h->L) * 16;
+        size_t b = (size_t)energy_blocks(h->L) * 8;
+        size_t c = (size_t)nmm * 32;
+        for (size_t v : {a, b, c}) need = need > v ? need : v;
+        h->part_bytes = need;
+    }
+    if ((s = dalloc(h, &h->part, h->part_bytes)) != MPR_OK) return bail(s);
+    if ((s = dalloc(h, &h->scal, 16 * 8)) != MPR_OK) return bail(s);
+    if ((s = dalloc(h, &h->z, (size_t)h->N * 8)) != MPR_OK) return bail(s);
+    if ((s = dalloc(h, &h->mask, (size_t)h->N)) != MPR_OK) return bail(s);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(h->z, values, (size_t)h->N * 8, kind, stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->mask, mask, (size_t)h->N, kind, stream) != cudaSuccess)
+        return bail(fail(MPR_ERR_CUDA, "input copy failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if (launch_minmax(h->z, h->mask, h->N, static_cast<double*>(h->part), nmm, h->scal, stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->host, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return bail(fail(MPR_ERR_CUDA, "range reduction failed: %s", cudaGetErrorString(cudaGetLastError())));
+    const double lo = h->host[0], hi = h->host[1], nmeas = h->host[2], bad = h->host[3];
+    if (bad > 0) return bail(fail(MPR_ERR_INVALID_ARG, "%.0f measured values are NaN or infinite", bad));
+    if (nmeas < 2 || !(hi > lo))
+        return bail(fail(MPR_ERR_DEGENERATE, "%.0f measured sites, range [%g, %g]", nmeas, lo, hi));
+    h->zmin = lo;
+    h->zmax = hi;
+    h->Np = h->N - (long long)nmeas;
+    h->launches += 2;   // range reduction
+    if ((s = init_state(h)) != MPR_OK) return bail(s);
+    *out = h;
+    return MPR_OK;
+}
+
+mpr_status ensure_eseries(mpr_ctx* h, int n)
+{
+    if (n <= h->eseries_cap) return MPR_OK;
+    dfree(h, &h->eseries, (size_t)h->eseries_cap * 8);
+    h->eseries_cap = 0;
+    CHECK(dalloc(h, &h->eseries, (size_t)n * 8));
+    h->eseries_cap = n;
+    return MPR_OK;
+}
+
+// n hybrid sweeps at temperature T; with kMeasure the raw bond sum of sweep k lands in
+// eseries[k]. Every launch goes to the handle's stream; nothing here synchronises.
+mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
+{
+    if (n <= 0) return MPR_OK;
+    if (flags & kMeasure) CHECK(ensure_eseries(h, n));
+    SweepArgs a{};
+    a.Lx = h->L.Lx;
+    a.Ly = h->L.Ly;
+    a.Lxh = h->L.Lxh;
+    a.pitch = h->L.pitch;
+    a.mpitch = h->L.mpitch;
+    a.flags = flags;
+    a.seed_lo = (uint32_t)h->opt.seed;
+    a.seed_hi = (uint32_t)(h->opt.seed >> 32);
+    a.problem = 0;
+    a.q = h->opt.q;
+    a.T = T;
+    a.invT = 1.0 / T;
+    a.epart = h->part;
+    const int nblk = sweep_blocks(h->L, h->prec);
+    const bool timed = h->prof && flags == 0;
+    if (timed) {
+        CHECK(harvest_profile(h));
+        CU(cudaEventRecord(h->ev0, h->stream));
+    }
+    for (int k = 0; k < n; ++k) {
+        a.sweep = h->sweep;
+        for (int c = 0; c < 2; ++c) {
+            a.colour = c;
+            a.own = h->ang[c];
+            a.other = h->ang[c ^ 1];
+            a.mbits = h->mb[c];
+            a.acc = h->acc[c];
+            a.acc_hi = h->acc_hi[c];
+            a.acc_lo = h->acc_lo[c];
+            CU(launch_sweep(h->prec, a, h->stream));
+        }
+        if (flags & kMeasure) CU(launch_reduce(h->prec, h->part, nblk, h->eseries + k, h->stream));
+        h->launches += (flags & kMeasure) ? 3 : 2;
+        ++h->sweep;
+        h->site_updates += (uint64_t)h->Np;
+    }
+    if (timed) {
+        CU(cudaEventRecord(h->ev1, h->stream));
+        h->prof_pending = true;
+        h->prof_pending_launches = 2ull * (uint64_t)n;
+    }
+    return MPR_OK;
+}
+
+// Mean over n measured sweeps of e_b = -raw/N_b, summed in sweep order on the host (FP64).
+mpr_status mean_energy(mpr_ctx* h, int n, double* mean)
+{
+    std::vector<double> raw((size_t)n);
+    CU(cudaMemcpyAsync(raw.data(), h->eseries, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CHECK(sync(h));
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += -raw[(size_t)k] / (double)h->Nb;
+    *mean = s / (double)n;
+    return MPR_OK;
+}
+
+mpr_status probe(mpr_ctx* h, double T, double* e)
+{
+    CHECK(sweeps(h, h->tune.n_eq, T, 0));
+    CHECK(sweeps(h, h->tune.n_meas, T, kMeasure));
+    return mean_energy(h, h->tune.n_meas, e);
+}
+
+}  // namespace
+
+extern "C" {
+
+mpr_status mpr_create(int Lx, int Ly, const double* values, const unsigned char* mask, mpr_handle* out)
+{
+    return create_common(Lx, Ly, values, mask, false, nullptr, out);
+}
+
+mpr_status mpr_create_dev(int Lx, int Ly, const double* values_dev, const unsigned char* mask_dev,
+                          void* stream, mpr_handle* out)
+{
+    return create_common(Lx, Ly, values_dev, mask_dev, true, static_cast<cudaStream_t>(stream), out);
+}
+
+void mpr_destroy(mpr_handle h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+mpr_status mpr_set_options(mpr_handle h, const mpr_options* opt)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    CHECK(validate_options(opt));
+    free_state(h);   // sizes depend on the old precision
+    h->opt = *opt;
+    if (h->opt.q == 0.0) h->opt.q = 0.5;
+    h->prec = Precision{opt->store, opt->energy, opt->func, opt->acc};
+    return init_state(h);
+}
+
+mpr_status mpr_get_options(mpr_handle h, mpr_options* opt)
+{
+    if (!h || !opt) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    *opt = h->opt;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_stream(mpr_handle h, void* stream)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    CHECK(sync(h));
+    h->stream = static_cast<cudaStream_t>(stream);
+    return MPR_OK;
+}
+
+mpr_status mpr_set_tuning(mpr_handle h, const mpr_tuning* t)
+{
+    if (!h || !t) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (t->n_eq < 0 || t->n_meas < 1 || !(t->T_lo > 0) || !(t->T_hi > t->T_lo) ||
+        !(t->rel_tol >= 0) || !(t->ratio_tol > 1.0) || t->max_probes < 2 || t->max_probes > 64)
+        return fail(MPR_ERR_INVALID_ARG, "tuning parameters out of range");
+    h->tune = *t;
+    return MPR_OK;
+}
+
+mpr_status mpr_tune_temperature(mpr_handle h, double* T_out)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    const mpr_tuning& t = h->tune;
+    const double e_s = h->e_s;
+    const double tol = t.rel_tol * fabs(e_s);
+    double lo = log(t.T_lo), hi = log(t.T_hi);
+    int np = 0;
+    mpr_status status = MPR_OK;
+    double T, e;
+
+    T = t.T_lo;
+    CHECK(probe(h, T, &e));
+    ++np;
+    if (fabs(e - e_s) <= tol || e_s < e) goto done;
+
+    T = t.T_hi;
+    CHECK(probe(h, T, &e));
+    ++np;
+    if (fabs(e - e_s) <= tol) goto done;
+    if (e_s > e) {
+        status = fail(MPR_ERR_TUNE_NO_CONVERGE, "sample energy %.6f above e_b(T_hi) = %.6f", e_s, e);
+        goto done;
+    }
+    for (;;) {
+        if (np >= t.max_probes) {
+            T = exp(0.5 * (lo + hi));
+            status = fail(MPR_ERR_TUNE_NO_CONVERGE, "no convergence in %d probes", np);
+            goto done;
+        }
+        const double mid = 0.5 * (lo + hi);
+        T = exp(mid);
+        CHECK(probe(h, T, &e));
+        ++np;
+        if (fabs(e - e_s) <= tol) goto done;
+        if (e < e_s) lo = mid; else hi = mid;
+        if (hi - lo < log(t.ratio_tol)) {
+            T = exp(0.5 * (lo + hi));
+            goto done;
+        }
+    }
+done:
+    h->T = T;
+    h->have_T = true;
+    h->n_probes = np;
+    if (T_out) *T_out = T;
+    return status;
+}
+
+mpr_status mpr_set_temperature(mpr_handle h, double T)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(T > 0.0) || !isfinite(T)) return fail(MPR_ERR_INVALID_ARG, "temperature %g must be > 0", T);
+    h->T = T;
+    h->have_T = true;
+    return MPR_OK;
+}
+
+mpr_status mpr_run(mpr_handle h, int equil, int samples)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (equil < 0 || samples < 0) return fail(MPR_ERR_INVALID_ARG, "negative sweep count");
+    if (!h->have_T) return fail(MPR_ERR_STATE, "no temperature: tune or set it first");
+    CHECK(sweeps(h, equil, h->T, 0));
+    if (samples > 0) {
+        CHECK(sweeps(h, samples, h->T, kSample | kMeasure));
+        h->nsamples += samples;
+        CHECK(mean_energy(h, samples, &h->e_bond_mean));
+    } else {
+        CHECK(sync(h));
+    }
+    return MPR_OK;
+}
+
+static mpr_status predict_to(mpr_handle h, double* out_dev)
+{
+    CU(launch_predict(h->L, h->prec, h->z, h->mask, h->scal, h->acc[0], h->acc[1], h->acc_hi[0],
+                      h->acc_lo[0], h->acc_hi[1], h->acc_lo[1], h->nsamples, out_dev, h->stream));
+    h->launches += 1;
+    return MPR_OK;
+}
+
+mpr_status mpr_predict(mpr_handle h, double* out)
+{
+    if (!h || !out) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (h->nsamples == 0) return fail(MPR_ERR_STATE, "no samples taken yet");
+    if (!h->tmpN) CHECK(dalloc(h, &h->tmpN, (size_t)h->N * 8));
+    CHECK(predict_to(h, h->tmpN));
+    CU(cudaMemcpyAsync(out, h->tmpN, (size_t)h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+    return sync(h);
+}
+
+mpr_status mpr_predict_dev(mpr_handle h, double* out_dev)
+{
+    if (!h || !out_dev) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (h->nsamples == 0) return fail(MPR_ERR_STATE, "no samples taken yet");
+    CHECK(predict_to(h, out_dev));
+    return sync(h);
+}
+
+mpr_status mpr_energy(mpr_handle h, double* e_bond, double* e_sample)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (e_bond) {
+        const int nb = energy_blocks(h->L);
+        CU(launch_energy_fp64(h->L, h->prec, h->ang[0], h->ang[1], h->opt.q,
+                              static_cast<double*>(h->part), nb, h->scal + 8, h->stream));
+        h->launches += 2;
+        CU(cudaMemcpyAsync(h->host + 8, h->scal + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CHECK(sync(h));
+        *e_bond = -h->host[8] / (double)h->Nb;
+    }
+    if (e_sample) *e_sample = h->e_s;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_info(mpr_handle h, mpr_info* info)
+{
+    if (!h || !info) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    info->Lx = h->L.Lx;
+    info->Ly = h->L.Ly;
+    info->n_sites = h->N;
+    info->n_pred = h->Np;
+    info->n_bonds = h->Nb;
+    info->n_sample_pairs = h->Nss;
+    info->zmin = h->zmin;
+    info->zmax = h->zmax;
+    info->e_sample = h->e_s;
+    info->T = h->have_T ? h->T : 0.0;
+    info->sweep = h->sweep;
+    info->n_samples = h->nsamples;
+    info->n_probes = h->n_probes;
+    info->e_bond_mean = h->e_bond_mean;
+    info->site_updates = h->site_updates;
+    info->device_bytes = h->bytes;
+    info->kernel_launches = h->launches;
+    info->prof_sweep_ms = h->prof_ms;
+    info->prof_sweep_launches = h->prof_launches;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_profiling(mpr_handle h, int on)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    CHECK(sync(h));
+    if (on && !h->ev0) {
+        CU(cudaEventCreate(&h->ev0));
+        CU(cudaEventCreate(&h->ev1));
+    }
+    h->prof = on != 0;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_state(mpr_handle h, double* angles, uint32_t* sweep)
+{
+    if (!h || !angles) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (!h->tmpN) CHECK(dalloc(h, &h->tmpN, (size_t)h->N * 8));
+    CU(launch_get_state(h->L, h->prec, h->ang[0], h->ang[1], h->tmpN, h->stream));
+    h->launches += 1;
+    CU(cudaMemcpyAsync(angles, h->tmpN, (size_t)h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+    CHECK(sync(h));
+    if (sweep) *sweep = h->sweep;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_state(mpr_handle h, const double* angles, uint32_t sweep)
+{
+    if (!h || !angles) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (!h->tmpN) CHECK(dalloc(h, &h->tmpN, (size_t)h->N * 8));
+    CU(cudaMemcpyAsync(h->tmpN, angles, (size_t)h->N * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(launch_set_state(h->L, h->prec, h->tmpN, h->mask, h->ang[0], h->ang[1], h->stream));
+    h->launches += 1;
+    CHECK(sync(h));
+    h->sweep = sweep;
+    return MPR_OK;
+}
+
+mpr_status mpr_philox4x32_10_dev(const uint32_t* ctr_dev, uint32_t* out_dev, int n, uint64_t seed,
+                                 void* stream)
+{
+    if (n < 0 || (n > 0 && (!ctr_dev || !out_dev)))
+        return fail(MPR_ERR_INVALID_ARG, "bad Philox arguments");
+    CU(launch_philox(ctr_dev, out_dev, n, seed, static_cast<cudaStream_t>(stream)));
+    CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return MPR_OK;
+}
+
+const char* mpr_status_string(mpr_status s)
+{
+    switch (s) {
+    case MPR_OK: return "ok";
+    case MPR_ERR_INVALID_ARG: return "invalid argument";
+    case MPR_ERR_DEGENERATE: return "degenerate data";
+    case MPR_ERR_NO_PAIRS: return "no measured nearest-neighbour pair";
+    case MPR_ERR_TUNE_NO_CONVERGE: return "temperature tuning did not converge";
+    case MPR_ERR_CUDA: return "CUDA error";
+    case MPR_ERR_OOM: return "out of device memory";
+    case MPR_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case MPR_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* mpr_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// mpr_internal.h -- host-side interface between the translation units of libmpr (kernel
+// launchers and the layout they share). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mpr {
+
+// Device layout of one problem. The lattice is split by colour c = (x + y) & 1 into two
+// half-lattices of Ly rows x pitch columns; site (x, y) of colour c sits at column j = x >> 1 of
+// row y (x = 2j + ((y + c) & 1)). Column j of a row exists when x < Lx; the rest is padding.
+// mbits[c] holds one bit per half-lattice entry (1 = measured/frozen or padding, 0 = update).
+struct Layout {
+    int Lx, Ly;
+    int Lxh;        // ceil(Lx / 2)
+    int pitch;      // entries per half-lattice row (multiple of 64)
+    int mpitch;     // 32-bit mask words per row = pitch / 32
+};
+
+enum Store : int { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+
+struct Precision {
+    int store;      // Store
+    int energy;     // 0 = FP64, 1 = FP32
+    int func;       // 0 = FP64, 1 = FP32 intrinsics
+    int acc;        // 0 = FP64, 1 = Kahan FP32
+};
+
+inline size_t store_bytes(int store) { return store == kF64 ? 8 : store == kF32 ? 4 : 2; }
+
+enum SweepFlags : int { kSample = 1, kMeasure = 2 };
+
+// One colour half-sweep of one problem.
+struct SweepArgs {
+    void* own;                 // half-lattice of the colour being updated
+    const void* other;         // the other colour
+    const uint32_t* mbits;     // mask words of the colour being updated
+    double* acc;               // FP64 accumulators of the colour (kSample, acc = FP64)
+    float* acc_hi;             // Kahan sum / compensation (kSample, acc = Kahan FP32)
+    float* acc_lo;
+    void* epart;               // per-block energy partials (kMeasure on colour 1), E type
+    int Lx, Ly, Lxh, pitch, mpitch;
+    int colour;
+    int flags;
+    uint32_t seed_lo, seed_hi, sweep, problem;
+    double q, T, invT;
+};
+
+// Launchers (all asynchronous on `st`); each returns the launch's cudaError_t.
+int sweep_blocks(const Layout& L, const Precision& p);
+cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st);
+
+cudaError_t launch_minmax(const double* z, const unsigned char* mask, long long N, double* part,
+                          int nblk, double* out4, cudaStream_t st);
+cudaError_t launch_init(const Layout& L, const Precision& p, const double* z,
+                        const unsigned char* mask, const double* range, void* ang0, void* ang1,
+                        uint32_t* mb0, uint32_t* mb1, uint64_t seed, uint32_t problem,
+                        cudaStream_t st);
+cudaError_t launch_sample_energy(const Layout& L, const double* z, const unsigned char* mask,
+                                 const double* range, double q, double* part_sum,
+                                 long long* part_cnt, int nblk, double* out2, cudaStream_t st);
+int sample_energy_blocks(const Layout& L);
+cudaError_t launch_energy_fp64(const Layout& L, const Precision& p, const void* ang0,
+                               const void* ang1, double q, double* part, int nblk, double* out,
+                               cudaStream_t st);
+int energy_blocks(const Layout& L);
+cudaError_t launch_reduce(const Precision& p, const void* part, int n, double* out,
+                          cudaStream_t st);
+cudaError_t launch_predict(const Layout& L, const Precision& p, const double* z,
+                           const unsigned char* mask, const double* range, const double* acc0,
+                           const double* acc1, const float* hi0, const float* lo0,
+                           const float* hi1, const float* lo1, int nsamples, double* out,
+                           cudaStream_t st);
+cudaError_t launch_get_state(const Layout& L, const Precision& p, const void* ang0,
+                             const void* ang1, double* out, cudaStream_t st);
+cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* in,
+                             const unsigned char* mask, void* ang0, void* ang1, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed,
+                          cudaStream_t st);
+
+}  // namespace mpr

@@ -1,0 +1,378 @@
+"""GPU-vs-oracle parity through the C ABI (Sec. 2: conditional hybrid MC on Eq. 2).
+
+Rules (the method is a stochastic iteration driven by counter-based random numbers, so the GPU
+and the oracle can be compared sweep by sweep from an identical state and Philox stream):
+  - integer work (Philox words, mask bits, counts) is bit-exact;
+  - FP64 (DDD) states agree to 1e-9 except at sites whose Metropolis margin |u - exp(-dE/T)| or
+    over-relaxation domain margin is below 1e-11 (a decision rounding can flip), and at the
+    black neighbours of such red sites;
+  - FP32 function setups use the oracle's 23-bit uniforms and agree to 1e-4 rad outside margins
+    of 1e-4; 16-bit storage setups start from states rounded to the storage type and agree to a
+    few storage ulps, with margins scaled by the storage ulp.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mpr_inputs
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2.0 * math.pi
+SETUPS_ALL = ["DDD", "SDS", "SSS", "SDD", "DDS", "HDS", "BDS", "HSS"]
+
+
+@pytest.fixture(scope="module")
+def mpr():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_08448_gb300 as m
+
+    m.load()
+    return m
+
+
+def _round_store(a, setup):
+    s = setup[0]
+    if s == "D":
+        return np.asarray(a, np.float64)
+    if s == "S":
+        return np.asarray(a, np.float32).astype(np.float64)
+    if s == "H":
+        return np.asarray(a, np.float16).astype(np.float64)
+    import torch
+
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _ulp_store(setup):
+    # spacing of the storage type in [4, 8), where angles near 2*pi live
+    return {"D": 2.0**-50, "S": 2.0**-21, "H": 2.0**-8, "B": 2.0**-5}[setup[0]]
+
+
+def _oracle(orc, Lx, Ly, seed, setup):
+    return orc.Oracle(Lx, Ly, seed=seed, ubits=32 if setup[2] == "D" else 23)
+
+
+def _neighbours(mask_bool):
+    out = np.zeros_like(mask_bool)
+    out[:, 1:] |= mask_bool[:, :-1]
+    out[:, :-1] |= mask_bool[:, 1:]
+    out[1:, :] |= mask_bool[:-1, :]
+    out[:-1, :] |= mask_bool[1:, :]
+    return out
+
+
+def _colour(Lx, Ly):
+    return (np.arange(Ly)[:, None] + np.arange(Lx)[None, :]) % 2
+
+
+# --- random numbers ------------------------------------------------------------------------
+
+def test_philox_bit_exact(mpr, orc):
+    import torch
+
+    rng = np.random.default_rng(0)
+    n = 20000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64)
+    seed = (0xDEADBEEF << 32) | 0x12345678
+    t = torch.from_numpy(ctr.astype(np.uint32).view(np.int32)).cuda()
+    out = mpr.mpr_philox4x32_10_dev(t, seed).cpu().numpy().view(np.uint32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(0, n, 7):
+        exp = orc.philox(32, 10, ctr[i], key)
+        assert np.array_equal(out[i].astype(np.uint64), exp), i
+
+
+# --- mapping, initial state, sample energy -------------------------------------------------
+
+SHAPES = [(64, 64, 0.33), (131, 37, 0.9), (3, 5, 0.4), (2, 7, 0.3), (257, 129, 0.66)]
+
+
+@pytest.mark.parametrize("Lx,Ly,p", SHAPES)
+@pytest.mark.parametrize("setup", ["DDD", "SDS", "HDS", "BDS"])
+def test_initial_state_matches_oracle(mpr, orc, Lx, Ly, p, setup):
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=Lx, mask_seed=Ly)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=123)
+        got, sweep = mpr.mpr_get_state(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    o = _oracle(orc, Lx, Ly, 123, setup)
+    phi, zmin, zmax = o.map(pr.z, pr.mask)
+    exp = _round_store(o.init(phi, pr.mask), setup)
+    assert sweep == 0
+    assert (info["zmin"], info["zmax"]) == (zmin, zmax)
+    assert info["n_pred"] == int((pr.mask == 0).sum())
+    if setup[0] == "B":
+        assert np.max(np.abs(got - exp)) <= 2.0**-5
+    else:
+        assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("Lx,Ly,p", SHAPES)
+def test_sample_energy_matches_oracle(mpr, orc, Lx, Ly, p):
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=2 * Lx, mask_seed=3 * Ly)
+    o = orc.Oracle(Lx, Ly)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    try:
+        e_s, n = o.energy_sample(phi, pr.mask)
+    except ValueError:
+        with pytest.raises(mpr.MPRError) as ei:
+            mpr.mpr_create(pr.z, pr.mask)
+        assert ei.value.status == mpr.MPR_ERR_NO_PAIRS
+        return
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        _, e_gpu = mpr.mpr_energy(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    assert info["n_sample_pairs"] == n
+    assert abs(e_gpu - e_s) <= 1e-13 * abs(e_s) + 1e-15
+
+
+# --- one sweep from an identical state -----------------------------------------------------
+
+def _start_state(orc, pr, setup, seed):
+    o = _oracle(orc, pr.Lx, pr.Ly, seed, setup)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    rng = np.random.default_rng(seed)
+    state = np.where(pr.mask == 1, phi, rng.random(pr.z.shape) * TWO_PI)
+    return o, _round_store(state, setup)
+
+
+def _gpu_sweeps(mpr, pr, setup, seed, state, sweep, T, equil, samples=0):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=seed)
+        mpr.mpr_set_state(h, state, sweep)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, equil, samples)
+        got, sw = mpr.mpr_get_state(h)
+        info = mpr.mpr_get_info(h)
+        zhat = mpr.mpr_predict(h) if samples else None
+        eb, _ = mpr.mpr_energy(h)
+    finally:
+        mpr.mpr_destroy(h)
+    return got, sw, info, zhat, eb
+
+
+@pytest.mark.parametrize("Lx,Ly,p", SHAPES)
+@pytest.mark.parametrize("T", [0.08, 1.0])
+def test_single_sweep_ddd(mpr, orc, Lx, Ly, p, T):
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=5, mask_seed=6)
+    o, state = _start_state(orc, pr, "DDD", 99)
+    got, sw, info, _, _ = _gpu_sweeps(mpr, pr, "DDD", 99, state, 17, T, 1)
+    exp, mm, om = o.sweep(state, pr.mask, T, 17, margins=True)
+    assert sw == 18 and info["site_updates"] == info["n_pred"]
+    bad = (mm < 1e-11) | (om < 1e-11)
+    excused = bad | (_neighbours(bad & (_colour(Lx, Ly) == 0)) & (_colour(Lx, Ly) == 1))
+    d = np.abs(got - exp)
+    assert np.all(d[~excused] <= 1e-9), d[~excused].max()
+    assert excused.sum() <= max(2, 1e-4 * Lx * Ly)
+    m = pr.mask == 1
+    assert np.array_equal(got[m].view(np.uint64), state[m].view(np.uint64))
+
+
+@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (257, 129, 0.66)])
+@pytest.mark.parametrize("setup", ["SDS", "SSS", "SDD", "DDS"])
+def test_single_sweep_fp32_functions(mpr, orc, Lx, Ly, p, setup):
+    T = 0.3
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=7, mask_seed=8)
+    o, state = _start_state(orc, pr, setup, 5)
+    got, _, _, _, _ = _gpu_sweeps(mpr, pr, setup, 5, state, 3, T, 1)
+    exp, mm, om = o.sweep(state, pr.mask, T, 3, margins=True)
+    thr = 1e-4 if (setup[2] == "S" or setup[0] != "D") else 1e-11
+    tol = 1e-4 if setup[2] == "S" or setup[0] == "S" else 1e-9
+    bad = (mm < thr) | (om < thr)
+    excused = bad | (_neighbours(bad & (_colour(Lx, Ly) == 0)) & (_colour(Lx, Ly) == 1))
+    d = np.abs(got - exp)
+    assert np.all(d[~excused] <= tol + 2 * _ulp_store(setup)), d[~excused].max()
+    assert excused.sum() <= max(3, 2e-3 * Lx * Ly)
+
+
+@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9)])
+@pytest.mark.parametrize("setup", ["HDS", "BDS", "HSS"])
+def test_single_sweep_16bit_storage(mpr, orc, Lx, Ly, p, setup):
+    # Red phase: identical inputs; the GPU result is its FP32 update rounded to the storage type.
+    # Black phase: against the oracle's black update on the oracle's own red result rounded to the
+    # storage type. Both sides round FP32/FP64 red results to the same 16-bit value except near a
+    # rounding boundary; black sites next to a red site where the two roundings differ are
+    # excused, like those next to a red decision within the margin.
+    T = 0.5
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=9, mask_seed=10)
+    o, state = _start_state(orc, pr, setup, 8)
+    got, _, _, _, _ = _gpu_sweeps(mpr, pr, setup, 8, state, 40, T, 1)
+    red, mm_r, om_r = o.half_sweep(state, pr.mask, T, 40, 0)
+    red_r = _round_store(red, setup)
+    col = _colour(Lx, Ly)
+    ulp = _ulp_store(setup)
+    bad_r = (mm_r < 1e-4) | (om_r < 1e-4)
+    sel = (col == 0) & ~bad_r
+    d = np.abs(got - red_r)
+    assert np.all(d[sel] <= ulp + 1e-4), d[sel].max()
+    differs = (col == 0) & (bad_r | (got != red_r))
+    assert differs.mean() < 0.01
+    blk, mm_b, om_b = o.half_sweep(red_r, pr.mask, T, 40, 1)
+    bad_b = (mm_b < 1e-4) | (om_b < 1e-4)
+    excused = bad_b | (_neighbours(differs) & (col == 1))
+    sel = (col == 1) & ~excused
+    d = np.abs(got - _round_store(blk, setup))
+    assert np.all(d[sel] <= ulp + 1e-4), d[sel].max()
+    assert excused[col == 1].mean() < 0.05
+
+
+# --- energies, trajectories, predictions ---------------------------------------------------
+
+@pytest.mark.parametrize("setup", ["DDD", "SDS", "HDS"])
+def test_bond_energy_of_state(mpr, orc, setup):
+    pr = mpr_inputs.make_problem(131, 37, 0.66, field_seed=11, mask_seed=12)
+    o, state = _start_state(orc, pr, setup, 3)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup)
+        mpr.mpr_set_state(h, state, 0)
+        eb, _ = mpr.mpr_energy(h)
+    finally:
+        mpr.mpr_destroy(h)
+    assert abs(eb - o.energy_bond(state)) < 1e-13
+
+
+def test_ddd_trajectory_prediction_and_energy(mpr, orc):
+    pr = mpr_inputs.make_problem(64, 64, 0.33, field_seed=13, mask_seed=14)
+    o, state = _start_state(orc, pr, "DDD", 21)
+    T, equil, ns = 0.25, 60, 20
+    got, sw, info, zhat, _ = _gpu_sweeps(mpr, pr, "DDD", 21, state, 0, T, equil, ns)
+    phi, zmin, zmax = o.map(pr.z, pr.mask)
+    st, _, _ = o.run(state, pr.mask, T, 0, equil)
+    st, acc, e = o.run(st, pr.mask, T, equil, ns, acc=np.zeros_like(st), energies=True)
+    exp_z = o.predict(acc, ns, pr.z, pr.mask, zmin, zmax)
+    pred = pr.mask == 0
+    close = np.abs(got - st) < 1e-9
+    assert close.mean() > 0.999
+    assert np.array_equal(zhat[~pred], pr.z[~pred])
+    assert np.mean(np.abs(zhat - exp_z)[pred] < 1e-7) > 0.999
+    if close.all():
+        assert abs(info["e_bond_mean"] - e.mean()) < 1e-12
+    assert sw == equil + ns and info["n_samples"] == ns
+
+
+@pytest.mark.parametrize("setup", SETUPS_ALL)
+@pytest.mark.parametrize("acc", ["f64", "kahan"])
+def test_frozen_sites_bit_exact_and_predictions_in_range(mpr, setup, acc):
+    pr = mpr_inputs.make_problem(131, 37, 0.66, field_seed=15, mask_seed=16)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=4, acc=acc)
+        before, _ = mpr.mpr_get_state(h)
+        mpr.mpr_set_temperature(h, 0.2)
+        mpr.mpr_run(h, 30, 10)
+        after, _ = mpr.mpr_get_state(h)
+        zhat = mpr.mpr_predict(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    m = pr.mask == 1
+    assert np.array_equal(after[m].view(np.uint64), before[m].view(np.uint64))
+    # angles stay in [0, 2*pi] as rounded to the storage type (FP32 rounds 2*pi up)
+    assert np.all((after >= 0) & (after <= _round_store(np.float32(TWO_PI), setup).max()))
+    assert np.array_equal(zhat[m], pr.z[m])
+    assert np.all((zhat >= info["zmin"] - 1e-9) & (zhat <= info["zmax"] + 1e-9))
+    assert np.isfinite(info["e_bond_mean"])
+
+
+def test_tuning_matches_oracle_ddd(mpr, orc):
+    pr = mpr_inputs.make_problem(48, 40, 0.33, field_seed=17, mask_seed=18)
+    kw = dict(n_eq=40, n_meas=20)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, "DDD", seed=6)
+        mpr.mpr_set_tuning(h, **kw)
+        T_gpu, st = mpr.mpr_tune_temperature(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    o = orc.Oracle(48, 40, seed=6)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    e_s, _ = o.energy_sample(phi, pr.mask)
+    st_o, T_o, _, sw, trace = o.tune(phi, pr.mask, e_s, 0, **kw)
+    assert st == st_o == 0
+    assert info["n_probes"] == len(trace) and info["sweep"] == sw
+    assert abs(T_gpu / T_o - 1.0) < 1e-9
+
+
+# --- edge cases ----------------------------------------------------------------------------
+
+def test_edge_cases(mpr):
+    z = np.arange(12, dtype=np.float64).reshape(3, 4)
+    with pytest.raises(mpr.MPRError) as e:
+        mpr.mpr_create(np.full((3, 4), 2.0), np.ones((3, 4)))
+    assert e.value.status == mpr.MPR_ERR_DEGENERATE
+    m = np.zeros((3, 4), np.uint8)
+    m[0, 0] = 1
+    with pytest.raises(mpr.MPRError) as e:
+        mpr.mpr_create(z, m)
+    assert e.value.status == mpr.MPR_ERR_DEGENERATE
+    m[2, 3] = 1
+    with pytest.raises(mpr.MPRError) as e:
+        mpr.mpr_create(z, m)
+    assert e.value.status == mpr.MPR_ERR_NO_PAIRS
+    bad = z.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(mpr.MPRError) as e:
+        mpr.mpr_create(bad, np.ones((3, 4)))
+    assert e.value.status == mpr.MPR_ERR_INVALID_ARG
+    # NaN at a prediction site is ignored
+    m2 = np.ones((3, 4), np.uint8)
+    m2[1, 1] = 0
+    h = mpr.mpr_create(np.where(m2 == 1, z, np.nan), m2)
+    try:
+        with pytest.raises(mpr.MPRError) as e:
+            mpr.mpr_run(h, 1, 1)
+        assert e.value.status == mpr.MPR_ERR_STATE
+        with pytest.raises(mpr.MPRError) as e:
+            mpr.mpr_predict(h)
+        assert e.value.status == mpr.MPR_ERR_STATE
+        mpr.mpr_set_temperature(h, 0.5)
+        mpr.mpr_run(h, 3, 2)
+        zh = mpr.mpr_predict(h)
+        assert np.isfinite(zh).all()
+    finally:
+        mpr.mpr_destroy(h)
+    # every site measured: nothing to update, prediction = data
+    h = mpr.mpr_create(z, np.ones((3, 4)))
+    try:
+        mpr.mpr_set_temperature(h, 0.5)
+        mpr.mpr_run(h, 2, 2)
+        assert np.array_equal(mpr.mpr_predict(h), z)
+        assert mpr.mpr_get_info(h)["site_updates"] == 0
+    finally:
+        mpr.mpr_destroy(h)
+
+
+def test_device_entry_points(mpr):
+    import torch
+
+    pr = mpr_inputs.make_problem(96, 80, 0.66, field_seed=19, mask_seed=20)
+    s = torch.cuda.Stream()
+    zt = torch.from_numpy(pr.z).cuda()
+    mt = torch.from_numpy(pr.mask).cuda()
+    h1 = mpr.mpr_create_dev(zt, mt, stream=s)
+    h2 = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        for h in (h1, h2):
+            mpr.mpr_set_options(h, "SDS", seed=3)
+            mpr.mpr_set_temperature(h, 0.3)
+            mpr.mpr_run(h, 20, 5)
+        out = torch.empty_like(zt)
+        mpr.mpr_predict_dev(h1, out)
+        assert np.array_equal(out.cpu().numpy(), mpr.mpr_predict(h2))
+    finally:
+        mpr.mpr_destroy(h1)
+        mpr.mpr_destroy(h2)
