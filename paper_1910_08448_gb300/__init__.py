@@ -97,6 +97,7 @@ def load():
             "mpr_get_state": ([H, vp, P(u32)], i),
             "mpr_set_state": ([H, vp, u32], i),
             "mpr_philox4x32_10_dev": ([vp, vp, i, u64, vp], i),
+            "mpr_bond_energy_noalloc": ([i, i, vp, d, vp, vp], i),
             "mpr_status_string": ([i], ctypes.c_char_p),
             "mpr_last_error": ([], ctypes.c_char_p),
         }
@@ -113,8 +114,8 @@ def exported_symbols():
     return ["mpr_create", "mpr_create_dev", "mpr_destroy", "mpr_set_options", "mpr_get_options",
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_run", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
-            "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling", "mpr_status_string",
-            "mpr_last_error"]
+            "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
+            "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error"]
 
 
 def _check(st: int, allow=()):
@@ -269,6 +270,18 @@ def mpr_philox4x32_10_dev(ctr, seed: int, stream=None):
     out = torch.empty_like(ctr)
     _check(load().mpr_philox4x32_10_dev(_tensor_ptr(ctr, "int32"), _tensor_ptr(out, "int32"),
                                         ctr.shape[0], int(seed), _stream_ptr(stream)))
+    return out
+
+
+def mpr_bond_energy_noalloc(angles, q: float, out, stream=None):
+    """Bond energy of a state held on the device, with no device allocation (for callers that
+    cannot allocate, e.g. inside CUDA-graph capture). angles: (Ly, Lx) float64 CUDA tensor;
+    out: float64 CUDA tensor of at least one element, written asynchronously on ``stream``."""
+    if angles.dim() != 2:
+        raise ValueError("angles must be a 2-D tensor (Ly, Lx)")
+    _check(load().mpr_bond_energy_noalloc(angles.shape[1], angles.shape[0],
+                                          _tensor_ptr(angles, "float64"), float(q),
+                                          _tensor_ptr(out, "float64"), _stream_ptr(stream)))
     return out
 
 

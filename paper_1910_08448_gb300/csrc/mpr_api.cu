@@ -663,3 +663,5 @@ const char* mpr_status_string(mpr_status s)
 const char* mpr_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+void mpr::set_last_error(const char* msg) { g_err = msg; }

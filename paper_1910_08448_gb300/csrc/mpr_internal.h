@@ -80,4 +80,7 @@ cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed,
                           cudaStream_t st);
 
+// Sets the message returned by mpr_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 }  // namespace mpr
