@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--acc", default="f64", choices=["f64", "kahan"])
     ap.add_argument("--equil", type=int, default=2000)
     ap.add_argument("--samples", type=int, default=200)
+    ap.add_argument("--tune-eq", type=int, default=200, help="sweeps per tuning probe before measuring")
+    ap.add_argument("--tune-meas", type=int, default=50, help="measured sweeps per tuning probe")
     ap.add_argument("--ddd-sweeps", type=int, default=10, help="FP64 sweeps timed for the speedup")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
@@ -202,7 +204,7 @@ def run_mine(args, dist: Dist):
     mpr.load()
     L, p = args.L, args.p
     pr = mpr_inputs.make_problem(L, L, p, field_seed=1 + dist.rank, mask_seed=101 + dist.rank,
-                                 device=dev)
+                                 periodic=L > 4096, device=dev)
     zt = torch.from_numpy(pr.z).to(dev)
     mt = torch.from_numpy(pr.mask).to(dev)
     out = torch.empty_like(zt)
@@ -213,6 +215,7 @@ def run_mine(args, dist: Dist):
         h = mpr.mpr_create_dev(zt, mt)
         try:
             mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+            mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
             if profile:
                 mpr.mpr_set_profiling(h, True)
             T, _ = mpr.mpr_tune_temperature(h)
@@ -319,6 +322,7 @@ def run_mine(args, dist: Dist):
             h = mpr.mpr_create(zn, mn)
             try:
                 mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+                mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
                 mpr.mpr_tune_temperature(h)
                 mpr.mpr_run(h, args.equil, args.samples)
                 mpr._check(lib.mpr_predict(h, on.ctypes.data_as(ctypes.c_void_p)))
@@ -381,6 +385,7 @@ def main():
                 f"{int(args.p * 100)}% removed: tune + {args.equil} equil + {args.samples} samples")
     config = {"workload": workload, "L": args.L, "p": args.p, "setup": args.setup,
               "acc": args.acc, "equil": args.equil, "samples": args.samples,
+              "tune_probe_sweeps": [args.tune_eq, args.tune_meas],
               "l2": "flushed between steps (512 MB write)"}
 
     if args.impl == "reference":

@@ -154,6 +154,47 @@ mpr_status mpr_set_state(mpr_handle h, const double* angles, uint32_t sweep);
 mpr_status mpr_philox4x32_10_dev(const uint32_t* ctr_dev, uint32_t* out_dev, int n, uint64_t seed,
                                  void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many independent problems of uneven size and sparsity in one persistent launch.
+ * Every problem runs the method of Sec. 2 (tuning, equilibration, sampling) with its own data,
+ * mask and temperature; problem i draws its random numbers from the Philox stream with problem id
+ * i (so problem 0 of a batch follows the same chain as a single handle with the same options).
+ * The batch computes with FP32 functions (opt->func must be MPR_PREC_S); storage, energy and
+ * accumulator precision are free. The whole fill is ONE cooperative kernel launch whose blocks
+ * meet at grid barriers between colour passes; a barrier wait is bounded (2 s by default) and a
+ * wait that runs out ends the launch with MPR_ERR_DEVICE_TIMEOUT (the batch is then unusable).
+ * --------------------------------------------------------------------------------------------- */
+typedef struct mpr_batch_ctx* mpr_batch;
+
+/* n problems; problem i has an Lx[i] x Ly[i] grid with host arrays values[i] and mask[i] as in
+ * mpr_create. opt may be NULL (defaults of mpr_create). Errors name the offending problem. */
+mpr_status mpr_batch_create(int n, const int* Lx, const int* Ly, const double* const* values,
+                            const unsigned char* const* mask, const mpr_options* opt,
+                            mpr_batch* out);
+void mpr_batch_destroy(mpr_batch b);
+mpr_status mpr_batch_set_stream(mpr_batch b, void* stream);
+mpr_status mpr_batch_set_tuning(mpr_batch b, const mpr_tuning* t);
+/* Launch shape: tile rows per warp (1, 2 or 4: tiles of 128 x 8*rows half-lattice entries),
+ * blocks per SM (0 = occupancy limit), and whether to launch through a one-node CUDA graph. */
+mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int use_graph);
+/* Autotuner: times `sweeps` sweeps of every launch shape on a copy of the batch state (the chains
+ * are left as they were), keeps the fastest, and caches it for batches of the same signature. */
+mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* blocks_per_sm_out);
+/* One launch: with T == NULL every problem is tuned first (as mpr_tune_temperature), else T[i]
+ * is used; then equil sweeps and samples accumulated sweeps (as mpr_run). T_out[i] and
+ * status_out[i] (either may be NULL) receive each problem's temperature and tuning status.
+ * Returns MPR_ERR_TUNE_NO_CONVERGE if any problem's tuning did not converge (results are still
+ * produced), MPR_ERR_DEVICE_TIMEOUT if a grid-barrier wait ran out. */
+mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, double* T_out,
+                          int* status_out);
+mpr_status mpr_batch_predict(mpr_batch b, int i, double* out);          /* host, Lx*Ly doubles */
+mpr_status mpr_batch_get_state(mpr_batch b, int i, double* angles, uint32_t* sweep);
+mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info);
+/* Fault injection for tests of the timeout path: the next fill expects `extra_arrivals` more
+ * blocks at every grid barrier than exist (so the first barrier cannot complete) and waits at most
+ * timeout_s seconds. Nothing faults or hangs: the launch ends and reports MPR_ERR_DEVICE_TIMEOUT. */
+mpr_status mpr_batch_inject_barrier_fault(mpr_batch b, int extra_arrivals, double timeout_s);
+
 /* mpr_bond_energy_noalloc: e_bond = -(1/N_b) sum_<ij> cos[q(phi_i - phi_j)] of a state the caller
  * holds on the device, computed without allocating any device memory. The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc -- code running

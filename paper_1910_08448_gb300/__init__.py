@@ -98,6 +98,17 @@ def load():
             "mpr_set_state": ([H, vp, u32], i),
             "mpr_philox4x32_10_dev": ([vp, vp, i, u64, vp], i),
             "mpr_bond_energy_noalloc": ([i, i, vp, d, vp, vp], i),
+            "mpr_batch_create": ([i, vp, vp, vp, vp, P(mpr_options), P(H)], i),
+            "mpr_batch_destroy": ([H], None),
+            "mpr_batch_set_stream": ([H, vp], i),
+            "mpr_batch_set_tuning": ([H, P(mpr_tuning)], i),
+            "mpr_batch_set_launch": ([H, i, i, i], i),
+            "mpr_batch_autotune": ([H, i, P(i), P(i)], i),
+            "mpr_batch_fill": ([H, vp, i, i, vp, vp], i),
+            "mpr_batch_predict": ([H, i, vp], i),
+            "mpr_batch_get_state": ([H, i, vp, P(u32)], i),
+            "mpr_batch_get_info": ([H, i, P(mpr_info)], i),
+            "mpr_batch_inject_barrier_fault": ([H, i, d], i),
             "mpr_status_string": ([i], ctypes.c_char_p),
             "mpr_last_error": ([], ctypes.c_char_p),
         }
@@ -115,7 +126,11 @@ def exported_symbols():
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_run", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
-            "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error"]
+            "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error",
+            "mpr_batch_create", "mpr_batch_destroy", "mpr_batch_set_stream",
+            "mpr_batch_set_tuning", "mpr_batch_set_launch", "mpr_batch_autotune",
+            "mpr_batch_fill", "mpr_batch_predict", "mpr_batch_get_state", "mpr_batch_get_info",
+            "mpr_batch_inject_barrier_fault"]
 
 
 def _check(st: int, allow=()):
@@ -283,6 +298,92 @@ def mpr_bond_energy_noalloc(angles, q: float, out, stream=None):
                                           _tensor_ptr(angles, "float64"), float(q),
                                           _tensor_ptr(out, "float64"), _stream_ptr(stream)))
     return out
+
+
+# --- batches ------------------------------------------------------------------------------------
+
+def mpr_batch_create(values_list, mask_list, setup: str = "SDS", seed: int = 0, q: float = 0.5,
+                     acc: str = "f64"):
+    """values_list / mask_list: sequences of (Ly_i, Lx_i) host arrays. Returns a batch handle."""
+    n = len(values_list)
+    if n != len(mask_list) or n == 0:
+        raise ValueError("need equally many value and mask arrays, at least one")
+    vs = [_f64_host(v) for v in values_list]
+    ms = [np.ascontiguousarray(m, dtype=np.uint8) for m in mask_list]
+    for v, m in zip(vs, ms):
+        if v.ndim != 2 or m.shape != v.shape:
+            raise ValueError("each problem needs 2-D values and mask of one shape")
+    Lx = (ctypes.c_int * n)(*[v.shape[1] for v in vs])
+    Ly = (ctypes.c_int * n)(*[v.shape[0] for v in vs])
+    vp = (ctypes.c_void_p * n)(*[v.ctypes.data for v in vs])
+    mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in ms])
+    o = make_options(setup, seed, q, acc)
+    b = ctypes.c_void_p()
+    _check(load().mpr_batch_create(n, Lx, Ly, vp, mp, ctypes.byref(o), ctypes.byref(b)))
+    b._n = n
+    return b
+
+
+def mpr_batch_destroy(b):
+    if b is not None and b.value:
+        load().mpr_batch_destroy(b)
+        b.value = None
+
+
+def mpr_batch_set_stream(b, stream):
+    _check(load().mpr_batch_set_stream(b, _stream_ptr(stream)))
+
+
+def mpr_batch_set_tuning(b, n_eq=200, n_meas=50, T_lo=1e-3, T_hi=10.0, rel_tol=1e-3,
+                         ratio_tol=1.001, max_probes=30):
+    t = mpr_tuning(n_eq, n_meas, T_lo, T_hi, rel_tol, ratio_tol, max_probes)
+    _check(load().mpr_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def mpr_batch_set_launch(b, rows: int = 2, blocks_per_sm: int = 0, use_graph: bool = False):
+    _check(load().mpr_batch_set_launch(b, rows, blocks_per_sm, int(bool(use_graph))))
+
+
+def mpr_batch_autotune(b, sweeps: int = 10):
+    r, k = ctypes.c_int(), ctypes.c_int()
+    _check(load().mpr_batch_autotune(b, sweeps, ctypes.byref(r), ctypes.byref(k)))
+    return r.value, k.value
+
+
+def mpr_batch_fill(b, equil: int, samples: int, T=None):
+    """One launch; T None = tune every problem. Returns (T array, status array)."""
+    n = b._n
+    Tin = None if T is None else np.ascontiguousarray(T, dtype=np.float64)
+    Tout = np.zeros(n)
+    st = np.zeros(n, dtype=np.int32)
+    _check(load().mpr_batch_fill(b, None if Tin is None else _ptr(Tin), equil, samples, _ptr(Tout),
+                                 _ptr(st)), allow=(MPR_ERR_TUNE_NO_CONVERGE,))
+    return Tout, st
+
+
+def mpr_batch_predict(b, i: int):
+    info = mpr_batch_get_info(b, i)
+    out = np.empty((info["Ly"], info["Lx"]))
+    _check(load().mpr_batch_predict(b, i, _ptr(out)))
+    return out
+
+
+def mpr_batch_get_state(b, i: int):
+    info = mpr_batch_get_info(b, i)
+    out = np.empty((info["Ly"], info["Lx"]))
+    sw = ctypes.c_uint32()
+    _check(load().mpr_batch_get_state(b, i, _ptr(out), ctypes.byref(sw)))
+    return out, sw.value
+
+
+def mpr_batch_get_info(b, i: int) -> dict:
+    info = mpr_info()
+    _check(load().mpr_batch_get_info(b, i, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in mpr_info._fields_}
+
+
+def mpr_batch_inject_barrier_fault(b, extra_arrivals: int = 1, timeout_s: float = 0.05):
+    _check(load().mpr_batch_inject_barrier_fault(b, extra_arrivals, float(timeout_s)))
 
 
 def mpr_status_string(st: int) -> str:

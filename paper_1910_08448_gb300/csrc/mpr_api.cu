@@ -268,7 +268,7 @@ mpr_status create_common(int Lx, int Ly, const double* values, const unsigned ch
     h->L.Lx = Lx;
     h->L.Ly = Ly;
     h->L.Lxh = (Lx + 1) / 2;
-    h->L.pitch = (h->L.Lxh + 63) / 64 * 64;
+    h->L.pitch = (h->L.Lxh + 127) / 128 * 128;
     h->L.mpitch = h->L.pitch / 32;
     h->N = (long long)Lx * Ly;
     h->Nb = (long long)Lx * (Ly - 1) + (long long)Ly * (Lx - 1);
@@ -284,9 +284,9 @@ mpr_status create_common(int Lx, int Ly, const double* values, const unsigned ch
     if (cudaMallocHost(&h->host, 16 * sizeof(double)) != cudaSuccess)
         return bail(fail(MPR_ERR_OOM, "pinned host allocation failed"));
     const int nmm = 256;
-    h->part_bytes = (size_t)sweep_blocks(h->L, h->prec);
     {
-        size_t need = h->part_bytes * 8;
+        const int sb = sweep_blocks(h->L, h->prec), sf = sweep_f32_blocks(h->L);
+        size_t need = (size_t)(sb > sf ? sb : sf) * 8;
         size_t a = (size_t)sample_energy_blocks(h->L) * 16;
         size_t b = (size_t)energy_blocks(h->L) * 8;
         size_t c = (size_t)nmm * 32;
@@ -340,7 +340,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.Lxh = h->L.Lxh;
     a.pitch = h->L.pitch;
     a.mpitch = h->L.mpitch;
-    a.flags = flags;
+    a.flags = flags | (h->prec.energy == 1 ? kEnergyF32 : 0);
     a.seed_lo = (uint32_t)h->opt.seed;
     a.seed_hi = (uint32_t)(h->opt.seed >> 32);
     a.problem = 0;
@@ -348,7 +348,8 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.T = T;
     a.invT = 1.0 / T;
     a.epart = h->part;
-    const int nblk = sweep_blocks(h->L, h->prec);
+    const bool f32 = h->prec.func == 1;
+    const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);
     const bool timed = h->prof && flags == 0;
     if (timed) {
         CHECK(harvest_profile(h));
@@ -364,7 +365,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
             a.acc = h->acc[c];
             a.acc_hi = h->acc_hi[c];
             a.acc_lo = h->acc_lo[c];
-            CU(launch_sweep(h->prec, a, h->stream));
+            CU(f32 ? launch_sweep_f32(h->prec, a, h->stream) : launch_sweep(h->prec, a, h->stream));
         }
         if (flags & kMeasure) CU(launch_reduce(h->prec, h->part, nblk, h->eseries + k, h->stream));
         h->launches += (flags & kMeasure) ? 3 : 2;

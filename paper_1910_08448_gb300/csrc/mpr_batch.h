@@ -1,0 +1,83 @@
+// mpr_batch.h -- device structures shared by the batched persistent kernel (mpr_batch.cu) and
+// its host driver (mpr_batch_api.cu). Not part of the public ABI.
+#pragma once
+
+#include "mpr_internal.h"
+
+namespace mpr {
+namespace batch {
+
+enum Phase : int { kProbeEquil = 0, kProbeMeasure = 1, kRunEquil = 2, kRunSample = 3, kDone = 4 };
+
+// Per-problem state that the kernel changes: the tuning state machine and the run counters.
+struct Dyn {
+    int phase;                  // Phase
+    int step;                   // sweeps done in the current phase
+    int np;                     // probes finished
+    int kind;                   // probe kind: 0 = T_lo, 1 = T_hi, 2 = bisection midpoint
+    int status;                 // MPR_OK or MPR_ERR_TUNE_NO_CONVERGE
+    int nsamples;               // sampling sweeps accumulated
+    unsigned sweep;             // Philox sweep index of the next sweep
+    unsigned pad_;
+    double T;                   // temperature of the current probe / of the run
+    double lo, hi, mid;         // bisection bracket in log T, current midpoint
+    double esum;                // sum of e_b over the measured sweeps of the current probe
+    double esamp;               // sum of e_b over the sampling sweeps
+    unsigned long long site_updates;
+};
+
+struct Prob {
+    // layout (fixed at creation)
+    int Lx, Ly, Lxh, pitch, mpitch;
+    int ntx, nty, ntiles, tile_base;
+    long long ang_off[2];       // element offsets into the angle pool (storage type)
+    long long mb_off[2];        // word offsets into the mask-bit pool
+    long long acc_off[2];       // element offsets into the accumulator pool(s)
+    long long Np;               // prediction sites
+    double Nb;                  // bonds
+    double e_s;                 // sample energy
+    unsigned tiles_done;        // black tiles finished in this sweep (arrival counter)
+    unsigned pad_;
+    Dyn d;
+};
+
+struct Ctl {
+    unsigned bar_count;         // grid barrier arrivals
+    unsigned bar_gen;           // grid barrier generation
+    int err;                    // 0, or MPR_ERR_DEVICE_TIMEOUT after a barrier wait ran out
+    int n_active;               // problems not yet done
+    long long timeout_ns;       // limit of one barrier wait
+    int bar_extra;              // fault injection: arrivals expected beyond the grid (0 normally)
+    int pad_;
+};
+
+struct Args {
+    Prob* prob;
+    int nprob;
+    const int* tile_prob;       // global tile index -> problem
+    int ntiles;
+    void* ang;
+    uint32_t* mb;
+    double* acc;                // FP64 accumulator pool (acc_kind 0)
+    float* acc_hi;              // Kahan pools (acc_kind 1)
+    float* acc_lo;
+    void* epart;                // one energy partial per tile
+    Ctl* ctl;
+    int n_eq, n_meas, max_probes;
+    int equil, samples;
+    int energy_f32, acc_kind;
+    int max_iters;
+    double T_lo, T_hi, rel_tol, log_ratio;
+    uint32_t seed_lo, seed_hi;
+    double q;
+};
+
+}  // namespace batch
+
+int batch_tile_rows(int rows);
+int batch_tile_cols();
+cudaError_t batch_occupancy(int store, int rows, int* blocks_per_sm);
+cudaError_t batch_launch(int store, int rows, int grid, const batch::Args& args, cudaStream_t st,
+                         bool use_graph);
+
+}  // namespace mpr

@@ -15,7 +15,7 @@ namespace mpr {
 struct Layout {
     int Lx, Ly;
     int Lxh;        // ceil(Lx / 2)
-    int pitch;      // entries per half-lattice row (multiple of 64)
+    int pitch;      // entries per half-lattice row (multiple of 128)
     int mpitch;     // 32-bit mask words per row = pitch / 32
 };
 
@@ -30,7 +30,7 @@ struct Precision {
 
 inline size_t store_bytes(int store) { return store == kF64 ? 8 : store == kF32 ? 4 : 2; }
 
-enum SweepFlags : int { kSample = 1, kMeasure = 2 };
+enum SweepFlags : int { kSample = 1, kMeasure = 2, kEnergyF32 = 4 };
 
 // One colour half-sweep of one problem.
 struct SweepArgs {
@@ -49,8 +49,11 @@ struct SweepArgs {
 };
 
 // Launchers (all asynchronous on `st`); each returns the launch's cudaError_t.
+// FP64-function setups (X_F = D): generic kernel; FP32-function setups: the FP32 kernel.
 int sweep_blocks(const Layout& L, const Precision& p);
 cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st);
+int sweep_f32_blocks(const Layout& L);
+cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st);
 
 cudaError_t launch_minmax(const double* z, const unsigned char* mask, long long N, double* part,
                           int nblk, double* out4, cudaStream_t st);
