@@ -347,6 +347,8 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.q = h->opt.q;
     a.T = T;
     a.invT = 1.0 / T;
+    a.qf = (float)h->opt.q;
+    a.invTf = (float)(1.0 / T);
     a.epart = h->part;
     const bool f32 = h->prec.func == 1;
     const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);

@@ -132,7 +132,7 @@ __device__ void load_dyn(const Prob& P, Dyn& d)
     d.status = __ldcg(&P.d.status);
     d.nsamples = __ldcg(&P.d.nsamples);
     d.sweep = __ldcg(&P.d.sweep);
-    d.pad_ = 0;
+    d.invTf = __ldcg(&P.d.invTf);
     d.T = __ldcg(&P.d.T);
     d.lo = __ldcg(&P.d.lo);
     d.hi = __ldcg(&P.d.hi);
@@ -191,6 +191,7 @@ __device__ void bookkeeping(Prob& P, const Args& A)
     default:
         break;
     }
+    d.invTf = (float)(1.0 / d.T);
     P.d = d;
     P.tiles_done = 0u;
 }
@@ -207,6 +208,7 @@ __device__ __forceinline__ void do_tile(const Args& A, int t, int colour, TileSm
     if (ph == kDone) return;
     const double T = __ldcg(&P.d.T);
     const unsigned sweep = __ldcg(&P.d.sweep);
+    const float invTf = __ldcg(&P.d.invTf);
     SweepArgs a;
     a.own = static_cast<char*>(A.ang) + (size_t)P.ang_off[colour] * sizeof(S);
     a.other = static_cast<const char*>(A.ang) + (size_t)P.ang_off[colour ^ 1] * sizeof(S);
@@ -228,7 +230,9 @@ __device__ __forceinline__ void do_tile(const Args& A, int t, int colour, TileSm
     a.problem = (uint32_t)p;
     a.q = A.q;
     a.T = T;
-    a.invT = 1.0 / T;
+    a.invT = 0.0;        // FP64 reciprocal not needed by the FP32 tile
+    a.qf = A.qf;
+    a.invTf = invTf;
     const int i = t - P.tile_base;
     const int tx = i % P.ntx, ty = i / P.ntx;
     const bool measure = colour == 1 && (ph == kProbeMeasure || ph == kRunSample);

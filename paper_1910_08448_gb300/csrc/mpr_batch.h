@@ -18,7 +18,7 @@ struct Dyn {
     int status;                 // MPR_OK or MPR_ERR_TUNE_NO_CONVERGE
     int nsamples;               // sampling sweeps accumulated
     unsigned sweep;             // Philox sweep index of the next sweep
-    unsigned pad_;
+    float invTf;                // 1/T in FP32 for the tile kernel
     double T;                   // temperature of the current probe / of the run
     double lo, hi, mid;         // bisection bracket in log T, current midpoint
     double esum;                // sum of e_b over the measured sweeps of the current probe
@@ -70,6 +70,7 @@ struct Args {
     double T_lo, T_hi, rel_tol, log_ratio;
     uint32_t seed_lo, seed_hi;
     double q;
+    float qf;
 };
 
 }  // namespace batch

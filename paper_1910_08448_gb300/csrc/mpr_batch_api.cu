@@ -221,6 +221,7 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.seed_lo = (uint32_t)b->opt.seed;
     A.seed_hi = (uint32_t)(b->opt.seed >> 32);
     A.q = b->opt.q;
+    A.qf = (float)b->opt.q;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms_out) {
         BCU(cudaEventCreate(&e0));
@@ -258,6 +259,7 @@ void prepare_fill(mpr_batch_ctx* b, const double* T)
 {
     for (int i = 0; i < b->n; ++i) {
         batch::Dyn& d = b->P[(size_t)i].d;
+        d.invTf = (float)(1.0 / (T ? T[i] : b->tune.T_lo));
         d.status = MPR_OK;
         d.esum = 0.0;
         d.esamp = 0.0;

@@ -46,6 +46,7 @@ struct SweepArgs {
     int flags;
     uint32_t seed_lo, seed_hi, sweep, problem;
     double q, T, invT;
+    float qf, invTf;           // the same in FP32 for the FP32-function kernel (no FP64 on device)
 };
 
 // Launchers (all asynchronous on `st`); each returns the launch's cudaError_t.

@@ -7,8 +7,7 @@
 // Tile: 128 half-lattice columns x (8 warps x R rows). A thread owns 4 consecutive columns of a
 // row (two same-colour site pairs -> two Philox calls), loaded and stored as one vector. The other
 // colour's tile and its one-site halo are staged in shared memory as unit vectors
-// (cos q*phi, sin q*phi), computed once per site and read by its four neighbours; column j of the
-// tile sits at shared column j - j0 + 2, so each lane's four interior entries are 16-B aligned.
+// (cos q*phi, sin q*phi), computed once per site and read by its four neighbours.
 #pragma once
 
 #include "mpr_device.cuh"
@@ -80,13 +79,26 @@ __device__ __forceinline__ void store4(S* p, const Pack4<S>& in)
     }
 }
 
+// Shared tile of the other colour as structure of arrays: column j of the tile at index
+// j - j0 + 4 (halo columns at 3 and kTJ + 4), so a lane's four interior columns form one aligned
+// 16-byte vector and a warp's vector accesses touch consecutive banks.
+constexpr int kSW = kTJ + 8;
 template <int R> struct TileSmem {
-    float2 nb[kWarps * R + 2][kTJ + 4];
+    float cs[kWarps * R + 2][kSW];
+    float sn[kWarps * R + 2][kSW];
     double wsum_d[kWarps];
     float wsum_f[kWarps];
 };
 
 template <int R> __host__ __device__ constexpr int tile_rows() { return kWarps * R; }
+
+// 2^x on the MUFU (hand-written PTX: ex2.approx.ftz.f32)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // One tile (tile column tx, tile row ty) of colour a.colour. SAMPLE: 0 none, 1 FP64 accumulators,
 // 2 Kahan FP32 accumulators. With MEASURE (black pass) the tile's sum of u_b . h_b over its
@@ -97,80 +109,95 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                                            void* eslot)
 {
     constexpr int TY = kWarps * R;
+    constexpr int NR = (TY + 2 + kWarps - 1) / kWarps;   // staged rows per warp
     const int c = a.colour, cb = c ^ 1;
     const int j0 = tx * kTJ;
     const int y0 = ty * TY;
     const int lane = threadIdx.x, warp = threadIdx.y;
     const S* __restrict__ other = static_cast<const S*>(a.other);
     S* __restrict__ own = static_cast<S*>(a.own);
-    const float q = (float)a.q;
+    const float q = a.qf;
+    const int jb = j0 + 4 * lane;             // first of this thread's 4 columns
+    const int lj = 4 * lane;
+
+    // ---- own rows: values and frozen bits, loaded before the staging so their latency overlaps
+    Pack4<S> mine[R];
+    uint32_t bits[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = y0 + warp * R + rr;
+        bits[rr] = 0xFu;
+        if (y < a.Ly) {
+            load4(own + (size_t)y * a.pitch + jb, mine[rr]);
+            bits[rr] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
+        }
+    }
 
     __syncthreads();   // the previous tile's readers are done with sm
-    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ) ----
-    for (int r = warp; r < TY + 2; r += kWarps) {
+    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ): loads first ----
+    Pack4<S> st[NR];
+    S halo[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = warp + i * kWarps;
+        const int y = y0 - 1 + r;
+        if (r < TY + 2 && y >= 0 && y < a.Ly) {
+            load4(other + (size_t)y * a.pitch + jb, st[i]);
+            if (lane < 2) {
+                const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
+                if (j >= 0 && 2 * j + ((y + cb) & 1) < a.Lx) halo[i] = other[(size_t)y * a.pitch + j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = warp + i * kWarps;
+        if (r >= TY + 2) break;
         const int y = y0 - 1 + r;
         const bool row_ok = y >= 0 && y < a.Ly;
         const int ob = (y + cb) & 1;
-        {   // interior: 4 consecutive columns per lane, one vector load
-            const int j = j0 + 4 * lane;
-            float2 v[4];
+        float vc[4], vs[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = make_float2(0.f, 0.f);
-            if (row_ok) {
-                Pack4<S> pk;
-                load4(other + (size_t)y * a.pitch + j, pk);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (2 * (j + k) + ob < a.Lx) {
-                        float sn, cs;
-                        __sincosf(q * load_as<float>(pk.s[k]), &sn, &cs);
-                        v[k] = make_float2(cs, sn);
-                    }
-                }
-            }
-            float4* dst = reinterpret_cast<float4*>(&sm.nb[r][2 + 4 * lane]);
-            dst[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-            dst[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        for (int k = 0; k < 4; ++k) {
+            vc[k] = 0.0f;
+            vs[k] = 0.0f;
+            if (row_ok && 2 * (jb + k) + ob < a.Lx) __sincosf(q * load_as<float>(st[i].s[k]), &vs[k], &vc[k]);
         }
-        if (lane < 2) {   // halo columns j0 - 1 and j0 + TJ
+        *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+        *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
             const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
-            const int cc = lane == 0 ? 1 : kTJ + 2;
-            float2 v = make_float2(0.f, 0.f);
-            if (row_ok && j >= 0 && 2 * j + ob < a.Lx) {
-                float sn, cs;
-                __sincosf(q * load_as<float>(other[(size_t)y * a.pitch + j]), &sn, &cs);
-                v = make_float2(cs, sn);
-            }
-            sm.nb[r][cc] = v;
+            const int cc = lane == 0 ? 3 : kTJ + 4;
+            float hc = 0.0f, hs = 0.0f;
+            if (row_ok && j >= 0 && 2 * j + ob < a.Lx) __sincosf(q * load_as<float>(halo[i]), &hs, &hc);
+            sm.cs[r][cc] = hc;
+            sm.sn[r][cc] = hs;
         }
     }
     __syncthreads();
 
-    const float invT = (float)a.invT;
+    const float nl2e_invT = -1.4426950408889634f * a.invTf;   // exp(-dE/T) = 2^(dE * nl2e_invT)
     const float two_pi = kTwoPiF;
     const float width = two_pi * q;
     const float inv_q = 1.0f / q;
     double e_d = 0.0;
     float e_f = 0.0f;
 
+#pragma unroll
     for (int rr = 0; rr < R; ++rr) {
         const int ly = warp * R + rr;
         const int y = y0 + ly;
         if (y >= a.Ly) break;
         const int o = (y + c) & 1;
-        const int jb = j0 + 4 * lane;           // first of this thread's 4 columns
-        const int lj = 4 * lane;
         const size_t idx = (size_t)y * a.pitch + jb;
-        const uint32_t bits = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
         bool ex[4], upd[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             ex[k] = 2 * (jb + k) + o < a.Lx;
-            upd[k] = ex[k] && !((bits >> k) & 1u);
+            upd[k] = ex[k] && !((bits[rr] >> k) & 1u);
         }
         if (!MEASURE && !(upd[0] || upd[1] || upd[2] || upd[3])) continue;
-        Pack4<S> pk;
-        load4(own + idx, pk);
+        Pack4<S>& pk = mine[rr];
         uint4 w[2];
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
@@ -179,13 +206,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                 w[pr] = pair_words((uint32_t)((jb >> 1) + pr), (uint32_t)y, a.sweep, a.problem,
                                    kTagMetropolis, (uint32_t)c, a.seed_lo, a.seed_hi);
         }
+        // neighbours: up/down rows at the same columns, the middle row at columns j+o-1, j+o
+        const float4 uc = *reinterpret_cast<const float4*>(&sm.cs[ly][4 + lj]);
+        const float4 us = *reinterpret_cast<const float4*>(&sm.sn[ly][4 + lj]);
+        const float4 dc = *reinterpret_cast<const float4*>(&sm.cs[ly + 2][4 + lj]);
+        const float4 ds = *reinterpret_cast<const float4*>(&sm.sn[ly + 2][4 + lj]);
+        const float4 mc4 = *reinterpret_cast<const float4*>(&sm.cs[ly + 1][4 + lj]);
+        const float4 ms4 = *reinterpret_cast<const float4*>(&sm.sn[ly + 1][4 + lj]);
+        const float ec = o ? sm.cs[ly + 1][8 + lj] : sm.cs[ly + 1][3 + lj];
+        const float es = o ? sm.sn[ly + 1][8 + lj] : sm.sn[ly + 1][3 + lj];
+        // middle row values m[0..4] = columns j+o-1 .. j+o+3 (site k: left m[k], right m[k+1])
+        const float mcv[5] = {o ? mc4.x : ec, o ? mc4.y : mc4.x, o ? mc4.z : mc4.y, o ? mc4.w : mc4.z, o ? ec : mc4.w};
+        const float msv[5] = {o ? ms4.x : es, o ? ms4.y : ms4.x, o ? ms4.z : ms4.y, o ? ms4.w : ms4.z, o ? es : ms4.w};
+        const float ucv[4] = {uc.x, uc.y, uc.z, uc.w}, usv[4] = {us.x, us.y, us.z, us.w};
+        const float dcv[4] = {dc.x, dc.y, dc.z, dc.w}, dsv[4] = {ds.x, ds.y, ds.z, ds.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             // local field h = sum of the neighbours' unit vectors (left, right, up, down)
-            const float2 lf = sm.nb[ly + 1][lj + k + o + 1], rt = sm.nb[ly + 1][lj + k + o + 2];
-            const float2 up = sm.nb[ly][lj + k + 2], dn = sm.nb[ly + 2][lj + k + 2];
-            const float hx = ((lf.x + rt.x) + up.x) + dn.x;
-            const float hy = ((lf.y + rt.y) + up.y) + dn.y;
+            const float hx = ((mcv[k] + mcv[k + 1]) + ucv[k]) + dcv[k];
+            const float hy = ((msv[k] + msv[k + 1]) + usv[k]) + dsv[k];
             float f = load_as<float>(pk.s[k]);
             if (upd[k]) {
                 const uint32_t wp = (k & 1) ? w[k >> 1].z : w[k >> 1].x;
@@ -198,7 +237,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                 __sincosf(q * fp, &sp, &cp);
                 // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
                 const float dE = hx * (c0 - cp) + hy * (s0 - sp);
-                const bool accept = dE <= 0.0f || u_acc < __expf(-dE * invT);
+                const bool accept = dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT);
                 const float f1 = accept ? fp : f;
                 // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q]
                 float fn = f1;

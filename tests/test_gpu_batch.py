@@ -69,7 +69,9 @@ def test_batch_single_sweep_matches_oracle_per_problem(mpr, orc, setup):
             bad_r = (col == 0) & ((mm_r < 1e-4) | (om_r < 1e-4))
             sel = (col == 0) & ~bad_r
             assert np.all(np.abs(got - red_r)[sel] <= ulp + 1e-4), i
-            differs = bad_r | ((col == 0) & (got != red_r))
+            # red sites whose stored result differs from the oracle's by more than FP32 error (a
+            # 16-bit rounding that went the other way): their black neighbours see other inputs
+            differs = bad_r | ((col == 0) & (np.abs(got - red_r) > 1e-4))
             assert differs.mean() < 0.01
             excused = ((col == 1) & ((mm_b < 1e-4) | (om_b < 1e-4))) | (_neighbours(differs) & (col == 1))
             sel = (col == 1) & ~excused

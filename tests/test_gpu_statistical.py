@@ -1,0 +1,113 @@
+"""Statistical parity over seeds (Sec. 3: AAE of Eq. 4 over prediction sites, mean over samples).
+
+Config 1 of the workload: 64 x 64 Gaussian fields (m = 50, sigma = 10, exponential covariance,
+kappa = 0.2), 33 % removed, temperature tuning, 1000 equilibration and 100 sampling sweeps; 10
+seeds. The FP64 oracle runs the same jobs. For every precision setup the seed-averaged MAE, RMSE
+and equilibrium bond energy must lie within 1 % of the oracle's; the measured gaps are printed.
+Larger configs compare reduced precision against the GPU FP64 (DDD) path.
+"""
+import numpy as np
+import pytest
+
+import mpr_inputs
+
+pytestmark = pytest.mark.gpu
+
+SEEDS = range(10)
+
+
+@pytest.fixture(scope="module")
+def mpr():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_08448_gb300 as m
+
+    m.load()
+    return m
+
+
+def _metrics(zhat, pr):
+    pred = pr.mask == 0
+    err = (zhat - pr.z)[pred]
+    return float(np.mean(np.abs(err))), float(np.sqrt(np.mean(err ** 2)))
+
+
+def _gpu_job(mpr, pr, setup, seed, equil, samples, acc="f64", T=None):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=seed, acc=acc)
+        if T is None:
+            T, _ = mpr.mpr_tune_temperature(h)
+        else:
+            mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, equil, samples)
+        zhat = mpr.mpr_predict(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    return zhat, info["e_bond_mean"], T
+
+
+@pytest.fixture(scope="module")
+def oracle_config1(orc):
+    out = []
+    for s in SEEDS:
+        pr = mpr_inputs.make_problem(64, 64, 0.33, field_seed=s, mask_seed=100 + s)
+        o = orc.Oracle(64, 64, seed=s)
+        r = o.gap_fill(pr.z, pr.mask, 1000, 100)
+        mae, rmse = _metrics(r["zhat"], pr)
+        out.append((pr, mae, rmse, float(np.mean(r["e_samples"])), r["T"]))
+    return out
+
+
+@pytest.mark.parametrize("setup,acc", [("DDD", "f64"), ("SDS", "f64"), ("SSS", "f64"),
+                                       ("HDS", "f64"), ("BDS", "f64"), ("SDS", "kahan"),
+                                       ("HSS", "kahan")])
+def test_config1_within_one_percent_of_oracle(mpr, orc, oracle_config1, setup, acc):
+    g_mae, g_rmse, g_e, o_mae, o_rmse, o_e = [], [], [], [], [], []
+    for s, (pr, mae, rmse, e, T) in zip(SEEDS, oracle_config1):
+        zhat, eb, Tg = _gpu_job(mpr, pr, setup, s, 1000, 100, acc)
+        m, r = _metrics(zhat, pr)
+        g_mae.append(m), g_rmse.append(r), g_e.append(eb)
+        o_mae.append(mae), o_rmse.append(rmse), o_e.append(e)
+    gaps = {k: abs(np.mean(a) / np.mean(b) - 1.0)
+            for k, a, b in (("mae", g_mae, o_mae), ("rmse", g_rmse, o_rmse), ("e_bond", g_e, o_e))}
+    print(f"\n{setup}/{acc}: MAE {np.mean(g_mae):.4f} vs {np.mean(o_mae):.4f}, gaps {gaps}")
+    for k, v in gaps.items():
+        assert v < 0.01, (k, v)
+
+
+def test_config2_reduced_precision_vs_fp64_gpu(mpr):
+    # 1024 x 1024, 66 % removed, 2000 + 200 sweeps: FP32 intrinsics (energy FP64) against DDD
+    gaps = []
+    for s in range(2):
+        pr = mpr_inputs.make_problem(1024, 1024, 0.66, field_seed=10 + s, mask_seed=20 + s)
+        zd, ed, Td = _gpu_job(mpr, pr, "DDD", s, 2000, 200)
+        zs, es, Ts = _gpu_job(mpr, pr, "SDS", s, 2000, 200)
+        md, _ = _metrics(zd, pr)
+        ms, _ = _metrics(zs, pr)
+        gaps.append((ms / md - 1.0, es / ed - 1.0, Ts / Td - 1.0))
+    g = np.mean(np.array(gaps), axis=0)
+    print(f"\nconfig 2 SDS vs DDD: MAE gap {g[0]:.2e}, e_bond gap {g[1]:.2e}, T gap {g[2]:.2e}")
+    assert abs(g[0]) < 0.01 and abs(g[1]) < 0.01
+
+
+@pytest.mark.parametrize("setup,acc", [("HDS", "f64"), ("BDS", "f64"), ("HDS", "kahan")])
+def test_config3_16bit_storage_vs_fp64_gpu(mpr, setup, acc):
+    # 4096 x 4096, 90 % removed, fixed temperature from one FP64 tuning, 400 + 100 sweeps
+    pr = mpr_inputs.make_problem(4096, 4096, 0.9, field_seed=1, mask_seed=101)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, "SDS", seed=3)
+        mpr.mpr_set_tuning(h, n_eq=100, n_meas=20)
+        T, _ = mpr.mpr_tune_temperature(h)
+    finally:
+        mpr.mpr_destroy(h)
+    zd, ed, _ = _gpu_job(mpr, pr, "DDD", 3, 400, 100, T=T)
+    zh, eh, _ = _gpu_job(mpr, pr, setup, 3, 400, 100, acc=acc, T=T)
+    md, rd = _metrics(zd, pr)
+    mh, rh = _metrics(zh, pr)
+    print(f"\nconfig 3 {setup}/{acc} vs DDD: MAE {mh:.4f} vs {md:.4f} ({mh / md - 1:.2e}), "
+          f"RMSE gap {rh / rd - 1:.2e}, e_bond gap {eh / ed - 1:.2e}")
+    assert abs(mh / md - 1.0) < 0.01 and abs(rh / rd - 1.0) < 0.01 and abs(eh / ed - 1.0) < 0.01
