@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", choices=["single", "batch"], default="single",
                     help="single: one L x L field; batch: many uneven problems in one launch")
     ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--no-autotune", action="store_true", help="batch: default launch shape")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -378,10 +379,17 @@ def run_batch(args, dist):
                              seed=7 + dist.rank, acc=args.acc)
     try:
         mpr.mpr_batch_set_tuning(b, n_eq=args.tune_eq, n_meas=args.tune_meas)
-        rows, bps = mpr.mpr_batch_autotune(b, 10)
+        if args.no_autotune:
+            rows, bps, mode = 2, 0, 2
+            mpr.mpr_batch_set_launch(b, rows, bps, mode)
+        else:
+            rows, bps, mode = mpr.mpr_batch_autotune(b, 10)
+
+        fills = []
 
         def step():
             T, st = mpr.mpr_batch_fill(b, args.equil, args.samples)
+            fills.append(mpr.mpr_batch_get_stats(b))
             for i, o in enumerate(outs):
                 mpr._check(lib.mpr_batch_predict(b, i, o.ctypes.data_as(ctypes.c_void_p)))
             return T, st
@@ -403,6 +411,12 @@ def run_batch(args, dist):
         dist.barrier()
         u1 = updates()
         launches = mpr.mpr_batch_get_info(b, 0)["kernel_launches"]
+        sweeps = [mpr.mpr_batch_get_info(b, i)["sweep"] for i in range(len(probs))]
+        # a fill with every problem at a fixed temperature: no tuning tail, equal sweeps
+        u_a = updates()
+        mpr.mpr_batch_fill(b, 200, 0, T=np.full(len(probs), 0.3))
+        fixed = mpr.mpr_batch_get_stats(b)
+        fixed_rate = (updates() - u_a) / (fixed["fill_ms"] / 1e3)
     finally:
         mpr.mpr_batch_destroy(b)
     ms = dist.max(dt * 1e3)
@@ -411,12 +425,14 @@ def run_batch(args, dist):
     for p, o in zip(probs, outs):
         pred = p.mask == 0
         maes.append(float(np.mean(np.abs(o - p.z)[pred])))
-    return {"value": upd / (ms / 1e3), "ms": ms, "rows": rows, "blocks_per_sm": bps,
+    return {"value": upd / (ms / 1e3), "ms": ms, "rows": rows, "blocks_per_sm": bps, "mode": mode,
             "clocks": clk.summary(), "n_problems": len(probs),
             "sites": int(sum(p.z.size for p in probs)),
             "pred_sites": int(sum(int((p.mask == 0).sum()) for p in probs)),
             "mean_mae": float(np.mean(maes)), "tune_status_nonzero": int(np.count_nonzero(st)),
-            "T_range": [float(np.min(T)), float(np.max(T))], "launches": launches}
+            "T_range": [float(np.min(T)), float(np.max(T))], "launches": launches,
+            "last_fill": fills[-1], "fixed_T_fill": dict(fixed, site_updates_per_s=fixed_rate),
+            "sweeps_per_problem": [int(np.min(sweeps)), int(np.median(sweeps)), int(np.max(sweeps))]}
 
 
 def oracle_sample(L, p, setup, seconds, seed=7, pr=None):
@@ -495,10 +511,15 @@ def main():
                            "setup": args.setup, "acc": args.acc, "sites": res["sites"],
                            "pred_sites": res["pred_sites"], "autotuned_rows": res["rows"],
                            "autotuned_blocks_per_sm": res["blocks_per_sm"],
+                           "autotuned_mode": ["persistent cooperative kernel",
+                                              "persistent kernel in a one-node graph",
+                                              "graph with device-side while loop"][res["mode"]],
                            "l2": "inputs larger than L2 (pooled state of all problems)"},
                 "clocks": res["clocks"], "gpu_launches": res["launches"],
                 "accuracy": {"mean_mae": res["mean_mae"], "T_range": res["T_range"],
                              "tune_not_converged": res["tune_status_nonzero"]},
+                "launch_stats": {"last_fill": res["last_fill"], "fixed_T_fill": res["fixed_T_fill"],
+                                 "sweeps_per_problem_min_med_max_cumulative": res["sweeps_per_problem"]},
             }
             print(json.dumps(line), flush=True)
         dist.close()

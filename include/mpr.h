@@ -175,10 +175,14 @@ void mpr_batch_destroy(mpr_batch b);
 mpr_status mpr_batch_set_stream(mpr_batch b, void* stream);
 mpr_status mpr_batch_set_tuning(mpr_batch b, const mpr_tuning* t);
 /* Launch shape: tile rows per warp (1, 2 or 4: tiles of 128 x 8*rows half-lattice entries),
- * blocks per SM (0 = occupancy limit), and whether to launch through a one-node CUDA graph. */
+ * blocks per SM (persistent modes; 0 = occupancy limit) and mode: 0 = one persistent cooperative
+ * kernel (blocks walk the tiles, grid barriers between colour passes), 1 = the same kernel as a
+ * one-node CUDA graph, 2 (default) = one CUDA graph whose device-side while loop repeats a red
+ * pass, a black pass (one block per tile) and a finish kernel until every problem is done. */
 mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int use_graph);
-/* Autotuner: times `sweeps` sweeps of every launch shape on a copy of the batch state (the chains
- * are left as they were), keeps the fastest, and caches it for batches of the same signature. */
+/* Autotuner: times `sweeps` sweeps of every launch shape and mode on a copy of the batch state
+ * (the chains are left as they were), keeps the fastest, and caches it for batches of the same
+ * signature. */
 mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* blocks_per_sm_out);
 /* One launch: with T == NULL every problem is tuned first (as mpr_tune_temperature), else T[i]
  * is used; then equil sweeps and samples accumulated sweeps (as mpr_run). T_out[i] and
@@ -190,6 +194,11 @@ mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, 
 mpr_status mpr_batch_predict(mpr_batch b, int i, double* out);          /* host, Lx*Ly doubles */
 mpr_status mpr_batch_get_state(mpr_batch b, int i, double* angles, uint32_t* sweep);
 mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info);
+/* The last fill's launch: iterations (sweeps of the longest-running problem), device time in ms
+ * (CUDA events on the batch's stream), and the launch shape and mode it used. Any pointer may be
+ * NULL. */
+mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* rows,
+                               int* blocks_per_sm, int* mode);
 /* Fault injection for tests of the timeout path: the next fill expects `extra_arrivals` more
  * blocks at every grid barrier than exist (so the first barrier cannot complete) and waits at most
  * timeout_s seconds. Nothing faults or hangs: the launch ends and reports MPR_ERR_DEVICE_TIMEOUT. */

@@ -108,6 +108,7 @@ def load():
             "mpr_batch_predict": ([H, i, vp], i),
             "mpr_batch_get_state": ([H, i, vp, P(u32)], i),
             "mpr_batch_get_info": ([H, i, P(mpr_info)], i),
+            "mpr_batch_get_stats": ([H, P(i), P(d), P(i), P(i), P(i)], i),
             "mpr_batch_inject_barrier_fault": ([H, i, d], i),
             "mpr_status_string": ([i], ctypes.c_char_p),
             "mpr_last_error": ([], ctypes.c_char_p),
@@ -130,6 +131,7 @@ def exported_symbols():
             "mpr_batch_create", "mpr_batch_destroy", "mpr_batch_set_stream",
             "mpr_batch_set_tuning", "mpr_batch_set_launch", "mpr_batch_autotune",
             "mpr_batch_fill", "mpr_batch_predict", "mpr_batch_get_state", "mpr_batch_get_info",
+            "mpr_batch_get_stats",
             "mpr_batch_inject_barrier_fault"]
 
 
@@ -340,14 +342,17 @@ def mpr_batch_set_tuning(b, n_eq=200, n_meas=50, T_lo=1e-3, T_hi=10.0, rel_tol=1
     _check(load().mpr_batch_set_tuning(b, ctypes.byref(t)))
 
 
-def mpr_batch_set_launch(b, rows: int = 2, blocks_per_sm: int = 0, use_graph: bool = False):
-    _check(load().mpr_batch_set_launch(b, rows, blocks_per_sm, int(bool(use_graph))))
+def mpr_batch_set_launch(b, rows: int = 2, blocks_per_sm: int = 0, mode: int = 2):
+    """mode 0: persistent cooperative kernel, 1: the same as a one-node graph, 2: graph with a
+    device-side while loop over per-pass kernels."""
+    _check(load().mpr_batch_set_launch(b, rows, blocks_per_sm, int(mode)))
 
 
 def mpr_batch_autotune(b, sweeps: int = 10):
+    """Returns (rows, blocks_per_sm, mode) of the fastest launch shape."""
     r, k = ctypes.c_int(), ctypes.c_int()
     _check(load().mpr_batch_autotune(b, sweeps, ctypes.byref(r), ctypes.byref(k)))
-    return r.value, k.value
+    return r.value, k.value, mpr_batch_get_stats(b)["mode"]
 
 
 def mpr_batch_fill(b, equil: int, samples: int, T=None):
@@ -380,6 +385,14 @@ def mpr_batch_get_info(b, i: int) -> dict:
     info = mpr_info()
     _check(load().mpr_batch_get_info(b, i, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in mpr_info._fields_}
+
+
+def mpr_batch_get_stats(b) -> dict:
+    it, ms, r, k, m = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().mpr_batch_get_stats(b, ctypes.byref(it), ctypes.byref(ms), ctypes.byref(r),
+                                      ctypes.byref(k), ctypes.byref(m)))
+    return {"iterations": it.value, "fill_ms": ms.value, "rows": r.value, "blocks_per_sm": k.value,
+            "mode": m.value}
 
 
 def mpr_batch_inject_barrier_fault(b, extra_arrivals: int = 1, timeout_s: float = 0.05):

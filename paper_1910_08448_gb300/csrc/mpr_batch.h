@@ -49,12 +49,19 @@ struct Ctl {
     long long timeout_ns;       // limit of one barrier wait
     int bar_extra;              // fault injection: arrivals expected beyond the grid (0 normally)
     int pad_;
+    unsigned work[2];           // next tile of the red / black pass (reset at the pass's barrier)
+    int list_sel;               // which of the two tile lists is current
+    int n_list;                 // tiles in the current list (tiles of unfinished problems)
+    int changed;                // a problem finished in this sweep: compact the list
+    int iters;                  // iterations (sweeps) the launch ran
 };
 
 struct Args {
     Prob* prob;
     int nprob;
     const int* tile_prob;       // global tile index -> problem
+    int* lists;                 // two tile lists of ntiles entries: the current one holds the
+                                // tiles of unfinished problems, largest first
     int ntiles;
     void* ang;
     uint32_t* mb;
@@ -77,8 +84,13 @@ struct Args {
 
 int batch_tile_rows(int rows);
 int batch_tile_cols();
+size_t batch_smem_bytes(int rows);
 cudaError_t batch_occupancy(int store, int rows, int* blocks_per_sm);
-cudaError_t batch_launch(int store, int rows, int grid, const batch::Args& args, cudaStream_t st,
+cudaError_t batch_launch(int store, int rows, int grid, const batch::Args* args_dev, cudaStream_t st,
                          bool use_graph);
+// Graph mode: an executable graph whose device-side while loop runs red pass, black pass and the
+// finish kernel until no problem is active (or max_iters). max_tiles = blocks of a pass kernel.
+cudaError_t batch_graph_build(int store, int rows, int max_tiles, const batch::Args* args_dev,
+                              cudaGraphExec_t* out);
 
 }  // namespace mpr

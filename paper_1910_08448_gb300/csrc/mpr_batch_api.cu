@@ -12,6 +12,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -52,7 +53,7 @@ mpr_status bfail(mpr_status s, const char* fmt, ...)
 
 // Launch shapes chosen by the autotuner, per batch signature, for the life of the process.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, long long, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, long long, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
 }  // namespace
 
@@ -64,10 +65,16 @@ struct mpr_batch_ctx {
     mpr_tuning tune{};
     cudaStream_t stream = nullptr;
     bool broken = false;
-    int rows = 2, bps = 0, use_graph = 0;    // launch shape (rows per warp, blocks per SM)
+    int rows = 2, bps = 0, use_graph = 2;    // launch shape (rows per warp, blocks per SM) and
+                                             // mode: 0/1 persistent kernel (direct / one-node
+                                             // graph), 2 graph with a device-side while loop
+    cudaGraphExec_t gexec[5] = {};           // graph-mode executables per rows (1, 2, 4)
+    int gexec_tiles[5] = {};
     int tiled_rows = 0;                      // rows of the current tile list
     int bar_extra = 0;
     double timeout_s = 2.0;
+    int last_iters = 0;                      // iterations of the last fill's launch
+    float last_ms = 0.f;                     // device time of the last fill's launch
     size_t bytes = 0;
     uint64_t launches = 0;
 
@@ -75,7 +82,10 @@ struct mpr_batch_ctx {
     std::vector<double> zmin, zmax;
     std::vector<long long> N, Nss, z_off;
     std::vector<int> tile_prob;
+    std::vector<int> order;                  // all tiles, largest first
+    std::vector<int> list;                   // tiles of the problems a fill starts with
     int ntiles = 0;
+    batch::Args* dArgs = nullptr;            // device copy of the launch arguments
 
     // device
     Prob* dP = nullptr;
@@ -119,7 +129,9 @@ mpr_status balloc(mpr_batch_ctx* b, T** p, size_t bytes)
 
 void bfree_all(mpr_batch_ctx* b)
 {
-    void* ptrs[] = {b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo,
+    for (auto& g : b->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    void* ptrs[] = {b->dArgs, b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo,
                     b->epart, b->zpool, b->mpool, b->range, b->scal, b->part, b->tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -136,27 +148,40 @@ Layout layout_of(const Prob& p)
     return L;
 }
 
-// Tile list for `rows` rows per warp: problem by problem, row-major tiles.
+// Tile list for `rows` rows per warp: problem by problem, row-major tiles; then the order in
+// which the blocks take them: by the number of lattice entries they cover, largest first.
 mpr_status build_tiles(mpr_batch_ctx* b, int rows)
 {
     if (b->tiled_rows == rows) return MPR_OK;
     const int TY = batch_tile_rows(rows), TJ = batch_tile_cols();
     b->tile_prob.clear();
+    std::vector<long long> cost;
     for (int i = 0; i < b->n; ++i) {
         Prob& p = b->P[(size_t)i];
         p.ntx = (p.Lxh + TJ - 1) / TJ;
         p.nty = (p.Ly + TY - 1) / TY;
         p.ntiles = p.ntx * p.nty;
         p.tile_base = (int)b->tile_prob.size();
-        for (int t = 0; t < p.ntiles; ++t) b->tile_prob.push_back(i);
+        for (int t = 0; t < p.ntiles; ++t) {
+            b->tile_prob.push_back(i);
+            const int tx = t % p.ntx, ty = t / p.ntx;
+            const long long w = std::min(TJ, p.Lxh - tx * TJ), h = std::min(TY, p.Ly - ty * TY);
+            cost.push_back(w * h);
+        }
     }
     b->ntiles = (int)b->tile_prob.size();
+    std::vector<int> order((size_t)b->ntiles);
+    for (int t = 0; t < b->ntiles; ++t) order[(size_t)t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return cost[(size_t)x] > cost[(size_t)y]; });
+    b->order = order;
     if (b->ntiles > b->tile_cap) {
         if (b->d_tile_prob) cudaFree(b->d_tile_prob);
         if (b->epart) cudaFree(b->epart);
         b->d_tile_prob = nullptr;
         b->epart = nullptr;
-        BCHECK(balloc(b, &b->d_tile_prob, (size_t)b->ntiles * sizeof(int)));
+        // tile -> problem, then the two tile lists
+        BCHECK(balloc(b, &b->d_tile_prob, 3 * (size_t)b->ntiles * sizeof(int)));
         BCHECK(balloc(b, &b->epart, (size_t)b->ntiles * sizeof(double)));
         b->tile_cap = b->ntiles;
     }
@@ -189,8 +214,16 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     for (int i = 0; i < b->n; ++i) active += b->P[(size_t)i].d.phase != batch::kDone;
     BCU(cudaMemcpyAsync(b->dP, b->P.data(), sizeof(Prob) * (size_t)b->n, cudaMemcpyHostToDevice,
                         b->stream));
+    b->list.clear();
+    for (int t : b->order)
+        if (b->P[(size_t)b->tile_prob[(size_t)t]].d.phase != batch::kDone) b->list.push_back(t);
+    if (!b->list.empty())
+        BCU(cudaMemcpyAsync(b->d_tile_prob + b->ntiles, b->list.data(), b->list.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream));
     batch::Ctl c{};
     c.n_active = active;
+    c.list_sel = 0;
+    c.n_list = (int)b->list.size();
     c.timeout_ns = (long long)(b->timeout_s * 1e9);
     c.bar_extra = b->bar_extra;
     BCU(cudaMemcpyAsync(b->ctl, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
@@ -198,6 +231,7 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.prob = b->dP;
     A.nprob = b->n;
     A.tile_prob = b->d_tile_prob;
+    A.lists = b->d_tile_prob + b->ntiles;
     A.ntiles = b->ntiles;
     A.ang = b->ang;
     A.mb = b->mb;
@@ -223,25 +257,38 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.q = b->opt.q;
     A.qf = (float)b->opt.q;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ms_out) {
-        BCU(cudaEventCreate(&e0));
-        BCU(cudaEventCreate(&e1));
-        BCU(cudaEventRecord(e0, b->stream));
-    }
+    BCU(cudaEventCreate(&e0));
+    BCU(cudaEventCreate(&e1));
+    BCU(cudaEventRecord(e0, b->stream));
     if (active > 0) {
-        BCU(batch_launch(b->prec.store, b->rows, grid, A, b->stream, b->use_graph != 0));
+        if (!b->dArgs) BCHECK(balloc(b, &b->dArgs, sizeof(batch::Args)));
+        BCU(cudaMemcpyAsync(b->dArgs, &A, sizeof A, cudaMemcpyHostToDevice, b->stream));
+        if (b->use_graph == 2) {
+            cudaGraphExec_t& ge = b->gexec[b->rows];
+            if (ge && b->gexec_tiles[b->rows] != b->ntiles) {
+                cudaGraphExecDestroy(ge);
+                ge = nullptr;
+            }
+            if (!ge) {
+                BCU(batch_graph_build(b->prec.store, b->rows, b->ntiles, b->dArgs, &ge));
+                b->gexec_tiles[b->rows] = b->ntiles;
+            }
+            BCU(cudaGraphLaunch(ge, b->stream));
+        } else {
+            BCU(batch_launch(b->prec.store, b->rows, grid, b->dArgs, b->stream, b->use_graph != 0));
+        }
         b->launches += 1;
     }
-    if (ms_out) BCU(cudaEventRecord(e1, b->stream));
+    BCU(cudaEventRecord(e1, b->stream));
     BCU(cudaMemcpyAsync(&c, b->ctl, sizeof c, cudaMemcpyDeviceToHost, b->stream));
     BCU(cudaMemcpyAsync(b->P.data(), b->dP, sizeof(Prob) * (size_t)b->n, cudaMemcpyDeviceToHost,
                         b->stream));
     BCU(cudaStreamSynchronize(b->stream));
-    if (ms_out) {
-        BCU(cudaEventElapsedTime(ms_out, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
+    BCU(cudaEventElapsedTime(&b->last_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms_out) *ms_out = b->last_ms;
+    b->last_iters = c.iters;
     b->bar_extra = 0;
     if (c.err) {
         b->broken = true;
@@ -481,6 +528,7 @@ mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int us
     BCU(batch_occupancy(b->prec.store, rows, &occ));
     if (blocks_per_sm < 0 || blocks_per_sm > occ)
         return bfail(MPR_ERR_INVALID_ARG, "blocks per SM must be in [0, %d] (0 = occupancy limit)", occ);
+    if (use_graph < 0 || use_graph > 2) return bfail(MPR_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
     b->rows = rows;
     b->bps = blocks_per_sm;
     b->use_graph = use_graph;
@@ -528,8 +576,9 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            b->rows = it->second.first;
-            b->bps = it->second.second;
+            b->rows = std::get<0>(it->second);
+            b->bps = std::get<1>(it->second);
+            b->use_graph = std::get<2>(it->second);
             if (rows_out) *rows_out = b->rows;
             if (blocks_per_sm_out) *blocks_per_sm_out = b->bps;
             return MPR_OK;
@@ -544,23 +593,39 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
     std::vector<double> T((size_t)b->n);
     for (int i = 0; i < b->n; ++i) T[(size_t)i] = keep[(size_t)i].d.T > 0 ? keep[(size_t)i].d.T : 0.5;
     float best = 1e30f;
-    int best_rows = b->rows, best_bps = b->bps;
+    int best_rows = b->rows, best_bps = b->bps, best_mode = b->use_graph;
     const int rows_c[3] = {1, 2, 4};
     mpr_status st = MPR_OK;
     for (int r : rows_c) {
+        // graph mode (one block per tile, device-side loop)
+        b->rows = r;
+        b->bps = 0;
+        b->use_graph = 2;
+        prepare_fill(b, T.data());
+        float ms = 0.f;
+        st = launch_fill(b, false, sweeps, 0, &ms);
+        if (st != MPR_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_rows = r;
+            best_bps = 0;
+            best_mode = 2;
+        }
+        // persistent cooperative kernel at every residency
         int occ = 0;
         if (batch_occupancy(b->prec.store, r, &occ) != cudaSuccess) continue;
         for (int bps = 1; bps <= occ; ++bps) {
             b->rows = r;
             b->bps = bps;
+            b->use_graph = 0;
             prepare_fill(b, T.data());
-            float ms = 0.f;
             st = launch_fill(b, false, sweeps, 0, &ms);
             if (st != MPR_OK) break;
             if (ms < best) {
                 best = ms;
                 best_rows = r;
                 best_bps = bps;
+                best_mode = 0;
             }
         }
         if (st != MPR_OK) break;
@@ -573,9 +638,10 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
     if (st != MPR_OK) return st;
     b->rows = best_rows;
     b->bps = best_bps;
+    b->use_graph = best_mode;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[key] = {best_rows, best_bps};
+        g_tune_cache[key] = std::make_tuple(best_rows, best_bps, best_mode);
     }
     if (rows_out) *rows_out = best_rows;
     if (blocks_per_sm_out) *blocks_per_sm_out = best_bps;
@@ -639,6 +705,18 @@ mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info)
     info->site_updates = p.d.site_updates;
     info->device_bytes = b->bytes;
     info->kernel_launches = b->launches;
+    return MPR_OK;
+}
+
+mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* rows,
+                               int* blocks_per_sm, int* mode)
+{
+    if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
+    if (mode) *mode = b->use_graph;
+    if (iterations) *iterations = b->last_iters;
+    if (fill_ms) *fill_ms = (double)b->last_ms;
+    if (rows) *rows = b->rows;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
     return MPR_OK;
 }
 
