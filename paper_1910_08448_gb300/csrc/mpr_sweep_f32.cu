@@ -10,7 +10,7 @@ using namespace f32;
 constexpr int kRows = 2;
 
 template <typename S, int R, bool MEASURE, int SAMPLE>
-__global__ void __launch_bounds__(256) sweep_f32_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, 4) sweep_f32_kernel(const SweepArgs a)
 {
     __shared__ __align__(16) TileSmem<R> sm;
     const int b = blockIdx.y * gridDim.x + blockIdx.x;

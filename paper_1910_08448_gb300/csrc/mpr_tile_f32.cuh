@@ -100,6 +100,60 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile as unit vectors
+// (cos q*phi, sin q*phi); entries outside the lattice are (0, 0) (open boundaries). All loads are
+// issued before the sin/cos work. CHECK = false when the caller knows every entry exists.
+template <typename S, int R, bool CHECK>
+__device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ other, int y0,
+                                      int j0, int jb, int lj, int cb, float q, TileSmem<R>& sm)
+{
+    constexpr int TY = kWarps * R;
+    constexpr int NR = (TY + 2 + kWarps - 1) / kWarps;   // staged rows per warp
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    Pack4<S> st[NR];
+    S halo[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = warp + i * kWarps;
+        const int y = y0 - 1 + r;
+        if (r < TY + 2 && (!CHECK || (y >= 0 && y < a.Ly))) {
+            load4(other + (size_t)y * a.pitch + jb, st[i]);
+            if (lane < 2) {
+                const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
+                if (!CHECK || (j >= 0 && 2 * j + ((y + cb) & 1) < a.Lx))
+                    halo[i] = other[(size_t)y * a.pitch + j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = warp + i * kWarps;
+        if (r >= TY + 2) break;
+        const int y = y0 - 1 + r;
+        const bool row_ok = !CHECK || (y >= 0 && y < a.Ly);
+        const int ob = (y + cb) & 1;
+        float vc[4], vs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            vc[k] = 0.0f;
+            vs[k] = 0.0f;
+            if (!CHECK || (row_ok && 2 * (jb + k) + ob < a.Lx))
+                __sincosf(q * load_as<float>(st[i].s[k]), &vs[k], &vc[k]);
+        }
+        *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+        *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
+            const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
+            const int cc = lane == 0 ? 3 : kTJ + 4;
+            float hc = 0.0f, hs = 0.0f;
+            if (!CHECK || (row_ok && j >= 0 && 2 * j + ob < a.Lx))
+                __sincosf(q * load_as<float>(halo[i]), &hs, &hc);
+            sm.cs[r][cc] = hc;
+            sm.sn[r][cc] = hs;
+        }
+    }
+}
+
 // One tile (tile column tx, tile row ty) of colour a.colour. SAMPLE: 0 none, 1 FP64 accumulators,
 // 2 Kahan FP32 accumulators. With MEASURE (black pass) the tile's sum of u_b . h_b over its
 // existing black sites is written by thread (0, 0) to *eslot (double, or float with kEnergyF32).
@@ -109,7 +163,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                                            void* eslot)
 {
     constexpr int TY = kWarps * R;
-    constexpr int NR = (TY + 2 + kWarps - 1) / kWarps;   // staged rows per warp
     const int c = a.colour, cb = c ^ 1;
     const int j0 = tx * kTJ;
     const int y0 = ty * TY;
@@ -134,46 +187,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
     }
 
     __syncthreads();   // the previous tile's readers are done with sm
-    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ): loads first ----
-    Pack4<S> st[NR];
-    S halo[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const int r = warp + i * kWarps;
-        const int y = y0 - 1 + r;
-        if (r < TY + 2 && y >= 0 && y < a.Ly) {
-            load4(other + (size_t)y * a.pitch + jb, st[i]);
-            if (lane < 2) {
-                const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
-                if (j >= 0 && 2 * j + ((y + cb) & 1) < a.Lx) halo[i] = other[(size_t)y * a.pitch + j];
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const int r = warp + i * kWarps;
-        if (r >= TY + 2) break;
-        const int y = y0 - 1 + r;
-        const bool row_ok = y >= 0 && y < a.Ly;
-        const int ob = (y + cb) & 1;
-        float vc[4], vs[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            vc[k] = 0.0f;
-            vs[k] = 0.0f;
-            if (row_ok && 2 * (jb + k) + ob < a.Lx) __sincosf(q * load_as<float>(st[i].s[k]), &vs[k], &vc[k]);
-        }
-        *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
-        *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
-            const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
-            const int cc = lane == 0 ? 3 : kTJ + 4;
-            float hc = 0.0f, hs = 0.0f;
-            if (row_ok && j >= 0 && 2 * j + ob < a.Lx) __sincosf(q * load_as<float>(halo[i]), &hs, &hc);
-            sm.cs[r][cc] = hc;
-            sm.sn[r][cc] = hs;
-        }
-    }
+    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
+    // lies inside the lattice (nearly all) skip the per-entry bounds checks.
+    const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
+    if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, q, sm);
+    else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, q, sm);
     __syncthreads();
 
     const float nl2e_invT = -1.4426950408889634f * a.invTf;   // exp(-dE/T) = 2^(dE * nl2e_invT)
@@ -196,16 +214,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
             ex[k] = 2 * (jb + k) + o < a.Lx;
             upd[k] = ex[k] && !((bits[rr] >> k) & 1u);
         }
-        if (!MEASURE && !(upd[0] || upd[1] || upd[2] || upd[3])) continue;
         Pack4<S>& pk = mine[rr];
+        // both Philox calls of the row, whether or not their sites update: no branch per site
         uint4 w[2];
 #pragma unroll
-        for (int pr = 0; pr < 2; ++pr) {
-            w[pr] = make_uint4(0u, 0u, 0u, 0u);
-            if (upd[2 * pr] || upd[2 * pr + 1])
-                w[pr] = pair_words((uint32_t)((jb >> 1) + pr), (uint32_t)y, a.sweep, a.problem,
-                                   kTagMetropolis, (uint32_t)c, a.seed_lo, a.seed_hi);
-        }
+        for (int pr = 0; pr < 2; ++pr)
+            w[pr] = pair_words((uint32_t)((jb >> 1) + pr), (uint32_t)y, a.sweep, a.problem,
+                               kTagMetropolis, (uint32_t)c, a.seed_lo, a.seed_hi);
         // neighbours: up/down rows at the same columns, the middle row at columns j+o-1, j+o
         const float4 uc = *reinterpret_cast<const float4*>(&sm.cs[ly][4 + lj]);
         const float4 us = *reinterpret_cast<const float4*>(&sm.sn[ly][4 + lj]);
@@ -226,7 +241,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
             const float hx = ((mcv[k] + mcv[k + 1]) + ucv[k]) + dcv[k];
             const float hy = ((msv[k] + msv[k + 1]) + usv[k]) + dsv[k];
             float f = load_as<float>(pk.s[k]);
-            if (upd[k]) {
+            {
+                // every site runs the move; frozen sites and padding discard the result below
                 const uint32_t wp = (k & 1) ? w[k >> 1].z : w[k >> 1].x;
                 const uint32_t wa = (k & 1) ? w[k >> 1].w : w[k >> 1].y;
                 const float u_prop = uniform_f(wp), u_acc = uniform_f(wa);
@@ -239,19 +255,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                 const float dE = hx * (c0 - cp) + hy * (s0 - sp);
                 const bool accept = dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT);
                 const float f1 = accept ? fp : f;
-                // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q]
-                float fn = f1;
-                if (hx != 0.0f || hy != 0.0f) {
-                    float r = 2.0f * atan2_fast(hy, hx) - q * f1;   // in [-2pi(1+q), 2pi]
-                    r = r < 0.0f ? r + two_pi : r;
-                    r = r < 0.0f ? r + two_pi : r;
-                    fn = r <= width ? r * inv_q : f1;
-                }
-                pk.s[k] = store_from<S>(fn);
-                f = load_as<float>(pk.s[k]);
-                if (SAMPLE == 1) {
-                    a.acc[idx + k] += (double)f;
-                } else if (SAMPLE == 2) {
+                // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
+                // h = 0 gives 0/0 = NaN in atan2_fast, every comparison below is false and the
+                // angle stays, as the move requires.
+                float r = 2.0f * atan2_fast(hy, hx) - q * f1;   // in [-2pi(1+q), 2pi]
+                r = r < 0.0f ? r + two_pi : r;
+                r = r < 0.0f ? r + two_pi : r;
+                const float fn = r <= width ? r * inv_q : f1;
+                const S stored = store_from<S>(fn);
+                pk.s[k] = upd[k] ? stored : pk.s[k];
+                f = upd[k] ? load_as<float>(stored) : f;
+            }
+            if (SAMPLE == 1) {
+                if (upd[k]) a.acc[idx + k] += (double)f;
+            } else if (SAMPLE == 2) {
+                if (upd[k]) {
                     // Kahan: hi carries the sum, lo the (negated) lost low-order part
                     const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
                     const float yv = f - lo;
@@ -268,7 +286,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
                 if (a.flags & kEnergyF32) e_f += e; else e_d += (double)e;
             }
         }
-        if (upd[0] || upd[1] || upd[2] || upd[3]) store4(own + idx, pk);
+        store4(own + idx, pk);   // unchanged entries are written back with their own bits
     }
 
     if (MEASURE) {
