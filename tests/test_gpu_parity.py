@@ -376,3 +376,63 @@ def test_device_entry_points(mpr):
     finally:
         mpr.mpr_destroy(h1)
         mpr.mpr_destroy(h2)
+
+
+# --- checkpoint / resume and other q -------------------------------------------------------
+
+@pytest.mark.parametrize("setup", ["DDD", "SDS", "HDS"])
+def test_checkpoint_resume_is_bit_exact(mpr, setup):
+    # counter-based random numbers: run(2n) == run(n); save; restore into a new handle; run(n)
+    pr = mpr_inputs.make_problem(131, 37, 0.66, field_seed=21, mask_seed=22)
+    T, n = 0.3, 25
+    h1 = mpr.mpr_create(pr.z, pr.mask)
+    h2 = mpr.mpr_create(pr.z, pr.mask)
+    h3 = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        for h in (h1, h2, h3):
+            mpr.mpr_set_options(h, setup, seed=11)
+            mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h1, 2 * n, 0)
+        full, sw_full = mpr.mpr_get_state(h1)
+        mpr.mpr_run(h2, n, 0)
+        half, sw_half = mpr.mpr_get_state(h2)
+        mpr.mpr_set_state(h3, half, sw_half)
+        mpr.mpr_run(h3, n, 0)
+        resumed, sw_res = mpr.mpr_get_state(h3)
+    finally:
+        for h in (h1, h2, h3):
+            mpr.mpr_destroy(h)
+    assert sw_full == sw_res == 2 * n
+    assert np.array_equal(full.view(np.uint64), resumed.view(np.uint64))
+
+
+@pytest.mark.parametrize("q", [0.3, 1.0])
+@pytest.mark.parametrize("setup", ["DDD", "SDS"])
+def test_single_sweep_other_q(mpr, orc, setup, q):
+    # the general over-relaxation (any q in (0, 1]; q = 1 is the planar rotator of Eq. 1)
+    T = 0.4
+    pr = mpr_inputs.make_problem(131, 37, 0.66, field_seed=23, mask_seed=24)
+    o = orc.Oracle(131, 37, seed=12, q=q, ubits=32 if setup[2] == "D" else 23)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    rng = np.random.default_rng(12)
+    state = _round_store(np.where(pr.mask == 1, phi, rng.random(pr.z.shape) * TWO_PI), setup)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=12, q=q)
+        mpr.mpr_set_state(h, state, 5)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, 1, 0)
+        got, _ = mpr.mpr_get_state(h)
+        e_gpu, e_s = mpr.mpr_energy(h)
+    finally:
+        mpr.mpr_destroy(h)
+    exp, mm, om = o.sweep(state, pr.mask, T, 5, margins=True)
+    thr = 1e-11 if setup == "DDD" else 1e-4
+    tol = 1e-9 if setup == "DDD" else 1e-4
+    bad = (mm < thr) | (om < thr)
+    col = _colour(131, 37)
+    excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
+    d = np.abs(got - exp)
+    assert np.all(d[~excused] <= tol + 2 * _ulp_store(setup)), d[~excused].max()
+    assert excused.mean() < 0.01
+    assert abs(e_s - o.energy_sample(phi, pr.mask)[0]) < 1e-12
