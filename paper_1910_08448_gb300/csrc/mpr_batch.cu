@@ -218,10 +218,9 @@ __device__ void bookkeeping(Prob& P, const Args& A, double raw)
 // not inlined, so every variant gets its own register allocation within the kernel's budget; the
 // arguments are a pointer and scalars, so nothing passes through local memory.
 template <typename S, int R, bool MEASURE, int SAMPLE>
-__device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int colour)
+__device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    const int p = A->tile_prob[t];
     const Prob& P = A->prob[p];
     SweepArgs a;
     a.own = static_cast<char*>(A->ang) + (size_t)P.ang_off[colour] * sizeof(S);
@@ -254,25 +253,33 @@ __device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int colo
                                       eslot);
 }
 
-template <typename S, int R>
-__device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int colour, TileSmem<R>& sm)
+template <typename S, int R, bool MEASURE, int SAMPLE>
+__device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour)
 {
-    const int p = A->tile_prob[t];
+    tile_body<S, R, MEASURE, SAMPLE>(A, t, p, colour);
+}
+
+// Tile t of problem p. The plain pass (no energy, no sampling: most passes) is inlined; the rarer
+// variants are calls.
+template <typename S, int R>
+__device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p, int colour,
+                                        TileSmem<R>& sm)
+{
     Prob& P = A->prob[p];
     const int ph = __ldcg(&P.d.phase);
     if (ph == kDone) return;
     const bool measure = colour == 1 && (ph == kProbeMeasure || ph == kRunSample);
     const bool sample = ph == kRunSample;
     if (!measure && !sample) {
-        tile_fn<S, R, false, 0>(A, t, colour);
+        tile_body<S, R, false, 0>(A, t, p, colour);
     } else if (measure && !sample) {
-        tile_fn<S, R, true, 0>(A, t, colour);
+        tile_fn<S, R, true, 0>(A, t, p, colour);
     } else if (!measure) {
-        if (A->acc_kind == 0) tile_fn<S, R, false, 1>(A, t, colour);
-        else tile_fn<S, R, false, 2>(A, t, colour);
+        if (A->acc_kind == 0) tile_fn<S, R, false, 1>(A, t, p, colour);
+        else tile_fn<S, R, false, 2>(A, t, p, colour);
     } else {
-        if (A->acc_kind == 0) tile_fn<S, R, true, 1>(A, t, colour);
-        else tile_fn<S, R, true, 2>(A, t, colour);
+        if (A->acc_kind == 0) tile_fn<S, R, true, 1>(A, t, p, colour);
+        else tile_fn<S, R, true, 2>(A, t, p, colour);
     }
     if (colour == 1) {
         __shared__ int s_last;
@@ -301,7 +308,7 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int c
 // tiles first, so uneven tiles and problems balance); the next index is fetched while the current
 // tile runs.
 template <typename S, int R>
-__device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const int* list, int n,
+__device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const int2* list, int n,
                                             int colour, TileSmem<R>& sm, volatile int* s_k)
 {
     if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
@@ -310,21 +317,22 @@ __device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const in
     while (k < n) {
         __syncthreads();   // every thread has read s_k
         if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
-        do_tile<S, R>(A, __ldcg(list + k), colour, sm);
+        const int2 e = __ldcg(list + k);
+        do_tile<S, R>(A, e.x, e.y, colour, sm);
         __syncthreads();
         k = *s_k;
     }
 }
 
 // Stable compaction of the active tile list (one block): drop the tiles of finished problems.
-__device__ void compact_list(const Args* __restrict__ A, const int* src, int n, int* dst, int* n_out,
+__device__ void compact_list(const Args* __restrict__ A, const int2* src, int n, int2* dst, int* n_out,
                              int* scan)
 {
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int per = (n + 255) / 256;
     const int b = tid * per, e = min(n, b + per);
     int cnt = 0;
-    for (int k = b; k < e; ++k) cnt += __ldcg(&A->prob[A->tile_prob[__ldcg(src + k)]].d.phase) != kDone;
+    for (int k = b; k < e; ++k) cnt += __ldcg(&A->prob[__ldcg(src + k).y].d.phase) != kDone;
     scan[tid] = cnt;
     __syncthreads();
     if (tid == 0) {
@@ -339,8 +347,8 @@ __device__ void compact_list(const Args* __restrict__ A, const int* src, int n, 
     __syncthreads();
     int o = scan[tid];
     for (int k = b; k < e; ++k) {
-        const int t = __ldcg(src + k);
-        if (__ldcg(&A->prob[A->tile_prob[t]].d.phase) != kDone) dst[o++] = t;
+        const int2 t = __ldcg(src + k);
+        if (__ldcg(&A->prob[t.y].d.phase) != kDone) dst[o++] = t;
     }
     __threadfence();
     __syncthreads();
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
     }
     __syncthreads();
     for (int it = 0; it < A->max_iters; ++it) {
-        const int* list = A->lists + (size_t)s_sel * A->ntiles;
+        const int2* list = A->lists + (size_t)s_sel * A->ntiles;
         const int n = s_n;
         colour_pass<S, R>(A, list, n, 0, sm, &s_k);
         if (!grid_barrier(ctl, expected, &s_err, &ctl->work[0])) return;
@@ -407,8 +415,8 @@ __global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A
     const Ctl* ctl = A->ctl;
     const int k = blockIdx.x;
     if (k >= __ldcg(&ctl->n_list)) return;
-    const int t = __ldcg(A->lists + (size_t)__ldcg(&ctl->list_sel) * A->ntiles + k);
-    do_tile<S, R>(A, t, colour, *reinterpret_cast<TileSmem<R>*>(dsm));
+    const int2 e = __ldcg(A->lists + (size_t)__ldcg(&ctl->list_sel) * A->ntiles + k);
+    do_tile<S, R>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R>*>(dsm));
 }
 
 __global__ void __launch_bounds__(256) finish_kernel(const Args* __restrict__ A,

@@ -60,8 +60,8 @@ struct Args {
     Prob* prob;
     int nprob;
     const int* tile_prob;       // global tile index -> problem
-    int* lists;                 // two tile lists of ntiles entries: the current one holds the
-                                // tiles of unfinished problems, largest first
+    int2* lists;                // two tile lists of ntiles (tile, problem) entries: the current
+                                // one holds the tiles of unfinished problems, largest first
     int ntiles;
     void* ang;
     uint32_t* mb;

@@ -83,7 +83,8 @@ struct mpr_batch_ctx {
     std::vector<long long> N, Nss, z_off;
     std::vector<int> tile_prob;
     std::vector<int> order;                  // all tiles, largest first
-    std::vector<int> list;                   // tiles of the problems a fill starts with
+    std::vector<int2> list;                  // (tile, problem) of the problems a fill starts with
+    int2* d_lists = nullptr;                 // the two device tile lists
     int ntiles = 0;
     batch::Args* dArgs = nullptr;            // device copy of the launch arguments
 
@@ -131,7 +132,7 @@ void bfree_all(mpr_batch_ctx* b)
 {
     for (auto& g : b->gexec)
         if (g) cudaGraphExecDestroy(g);
-    void* ptrs[] = {b->dArgs, b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo,
+    void* ptrs[] = {b->d_lists, b->dArgs, b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo,
                     b->epart, b->zpool, b->mpool, b->range, b->scal, b->part, b->tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -177,11 +178,13 @@ mpr_status build_tiles(mpr_batch_ctx* b, int rows)
     b->order = order;
     if (b->ntiles > b->tile_cap) {
         if (b->d_tile_prob) cudaFree(b->d_tile_prob);
+        if (b->d_lists) cudaFree(b->d_lists);
         if (b->epart) cudaFree(b->epart);
         b->d_tile_prob = nullptr;
+        b->d_lists = nullptr;
         b->epart = nullptr;
-        // tile -> problem, then the two tile lists
-        BCHECK(balloc(b, &b->d_tile_prob, 3 * (size_t)b->ntiles * sizeof(int)));
+        BCHECK(balloc(b, &b->d_tile_prob, (size_t)b->ntiles * sizeof(int)));
+        BCHECK(balloc(b, &b->d_lists, 2 * (size_t)b->ntiles * sizeof(int2)));
         BCHECK(balloc(b, &b->epart, (size_t)b->ntiles * sizeof(double)));
         b->tile_cap = b->ntiles;
     }
@@ -215,10 +218,12 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     BCU(cudaMemcpyAsync(b->dP, b->P.data(), sizeof(Prob) * (size_t)b->n, cudaMemcpyHostToDevice,
                         b->stream));
     b->list.clear();
-    for (int t : b->order)
-        if (b->P[(size_t)b->tile_prob[(size_t)t]].d.phase != batch::kDone) b->list.push_back(t);
+    for (int t : b->order) {
+        const int p = b->tile_prob[(size_t)t];
+        if (b->P[(size_t)p].d.phase != batch::kDone) b->list.push_back(make_int2(t, p));
+    }
     if (!b->list.empty())
-        BCU(cudaMemcpyAsync(b->d_tile_prob + b->ntiles, b->list.data(), b->list.size() * sizeof(int),
+        BCU(cudaMemcpyAsync(b->d_lists, b->list.data(), b->list.size() * sizeof(int2),
                             cudaMemcpyHostToDevice, b->stream));
     batch::Ctl c{};
     c.n_active = active;
@@ -231,7 +236,7 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.prob = b->dP;
     A.nprob = b->n;
     A.tile_prob = b->d_tile_prob;
-    A.lists = b->d_tile_prob + b->ntiles;
+    A.lists = b->d_lists;
     A.ntiles = b->ntiles;
     A.ang = b->ang;
     A.mb = b->mb;
