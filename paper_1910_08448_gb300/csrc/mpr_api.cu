@@ -407,6 +407,7 @@ extern "C" {
 
 mpr_status mpr_create(int Lx, int Ly, const double* values, const unsigned char* mask, mpr_handle* out)
 {
+    NvtxRange r("mpr_create");
     return create_common(Lx, Ly, values, mask, false, nullptr, out);
 }
 
@@ -462,6 +463,7 @@ mpr_status mpr_set_tuning(mpr_handle h, const mpr_tuning* t)
 
 mpr_status mpr_tune_temperature(mpr_handle h, double* T_out)
 {
+    NvtxRange r("mpr_tune_temperature");
     if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
     const mpr_tuning& t = h->tune;
     const double e_s = h->e_s;
@@ -520,6 +522,7 @@ mpr_status mpr_set_temperature(mpr_handle h, double T)
 
 mpr_status mpr_run(mpr_handle h, int equil, int samples)
 {
+    NvtxRange r("mpr_run");
     if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
     if (equil < 0 || samples < 0) return fail(MPR_ERR_INVALID_ARG, "negative sweep count");
     if (!h->have_T) return fail(MPR_ERR_STATE, "no temperature: tune or set it first");
@@ -544,6 +547,7 @@ static mpr_status predict_to(mpr_handle h, double* out_dev)
 
 mpr_status mpr_predict(mpr_handle h, double* out)
 {
+    NvtxRange r("mpr_predict");
     if (!h || !out) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
     if (h->nsamples == 0) return fail(MPR_ERR_STATE, "no samples taken yet");
     if (!h->tmpN) CHECK(dalloc(h, &h->tmpN, (size_t)h->N * 8));

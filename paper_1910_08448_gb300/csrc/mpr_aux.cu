@@ -82,34 +82,35 @@ __global__ void __launch_bounds__(kThreads) init_kernel(Layout L, const double* 
 {
     const int j = blockIdx.x * kThreads + threadIdx.x;
     if (j >= L.pitch) return;   // pitch is a multiple of 32: whole warps leave together
-    const int y = blockIdx.y;
     const int c = blockIdx.z;
-    const int x = 2 * j + ((y + c) & 1);
-    S* ang = c ? ang1 : ang0;
-    uint32_t* mb = c ? mb1 : mb0;
-    const size_t idx = (size_t)y * L.pitch + j;
-    bool frozen = true;   // padding counts as frozen: never updated
-    if (x < L.Lx) {
-        const size_t s = (size_t)y * L.Lx + x;
-        double phi;
-        if (mask[s]) {
-            const double lo = range[0], hi = range[1];
-            const double t = (z[s] - lo) / (hi - lo);
-            phi = kTwoPi * t;
+    for (int y = blockIdx.y; y < L.Ly; y += gridDim.y) {   // rows beyond the 65535 grid limit
+        const int x = 2 * j + ((y + c) & 1);
+        S* ang = c ? ang1 : ang0;
+        uint32_t* mb = c ? mb1 : mb0;
+        const size_t idx = (size_t)y * L.pitch + j;
+        bool frozen = true;   // padding counts as frozen: never updated
+        if (x < L.Lx) {
+            const size_t s = (size_t)y * L.Lx + x;
+            double phi;
+            if (mask[s]) {
+                const double lo = range[0], hi = range[1];
+                const double t = (z[s] - lo) / (hi - lo);
+                phi = kTwoPi * t;
+            } else {
+                frozen = false;
+                const uint4 w = pair_words((uint32_t)(j >> 1), (uint32_t)y, 0u, problem, kTagInit,
+                                           (uint32_t)c, seed_lo, seed_hi);
+                const uint32_t wp = (j & 1) ? w.z : w.x;
+                const double u = fp32_uniform ? (double)uniform_f(wp) : uniform_d(wp);
+                phi = kTwoPi * u;
+            }
+            ang[idx] = store_from<S>(phi);
         } else {
-            frozen = false;
-            const uint4 w = pair_words((uint32_t)(j >> 1), (uint32_t)y, 0u, problem, kTagInit,
-                                       (uint32_t)c, seed_lo, seed_hi);
-            const uint32_t wp = (j & 1) ? w.z : w.x;
-            const double u = fp32_uniform ? (double)uniform_f(wp) : uniform_d(wp);
-            phi = kTwoPi * u;
+            ang[idx] = store_from<S>(0.0);
         }
-        ang[idx] = store_from<S>(phi);
-    } else {
-        ang[idx] = store_from<S>(0.0);
+        const uint32_t bits = __ballot_sync(0xffffffffu, frozen);
+        if ((threadIdx.x & 31) == 0) mb[(size_t)y * L.mpitch + (j >> 5)] = bits;
     }
-    const uint32_t bits = __ballot_sync(0xffffffffu, frozen);
-    if ((threadIdx.x & 31) == 0) mb[(size_t)y * L.mpitch + (j >> 5)] = bits;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -331,7 +332,7 @@ cudaError_t launch_init(const Layout& L, const Precision& p, const double* z,
                         uint32_t* mb0, uint32_t* mb1, uint64_t seed, uint32_t problem,
                         cudaStream_t st)
 {
-    const dim3 grid((L.pitch + kThreads - 1) / kThreads, L.Ly, 2);
+    const dim3 grid((L.pitch + kThreads - 1) / kThreads, L.Ly < 65535 ? L.Ly : 65535, 2);
     const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
     return dispatch_store(p.store, [&](auto tag) {
         using S = decltype(tag);

@@ -543,6 +543,7 @@ mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int us
 mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, double* T_out,
                           int* status_out)
 {
+    NvtxRange r("mpr_batch_fill");
     if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
     if (b->broken) return bfail(MPR_ERR_STATE, "the batch was left undefined by a device timeout");
     if (equil < 0 || samples < 0) return bfail(MPR_ERR_INVALID_ARG, "negative sweep count");

@@ -3,10 +3,19 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 namespace mpr {
+
+// NVTX range for the lifetime of a scope (visible in Nsight tools; costs nothing without one).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device layout of one problem. The lattice is split by colour c = (x + y) & 1 into two
 // half-lattices of Ly rows x pitch columns; site (x, y) of colour c sits at column j = x >> 1 of

@@ -38,8 +38,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
     __shared__ E wsum[kWarps];
 
     const int c = a.colour, cb = c ^ 1;
-    const int j0 = blockIdx.x * kTJ;
-    const int y0 = blockIdx.y * TY;
+    // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
+    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    const int j0 = (int)(blockIdx.x % ntx) * kTJ;
+    const int y0 = (int)(blockIdx.x / ntx) * TY;
     const S* __restrict__ other = static_cast<const S*>(a.other);
     S* __restrict__ own = static_cast<S*>(a.own);
     const F q = (F)a.q;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         if (tid == 0) {
             E s = (E)0;
             for (int i = 0; i < kWarps; ++i) s += wsum[i];
-            static_cast<E*>(a.epart)[blockIdx.y * gridDim.x + blockIdx.x] = s;
+            static_cast<E*>(a.epart)[blockIdx.x] = s;
         }
     }
 }
@@ -162,7 +164,7 @@ constexpr int kRows = 2;
 template <typename S, typename F, typename E>
 cudaError_t launch_typed(const SweepArgs& a, cudaStream_t st)
 {
-    dim3 grid((a.Lxh + kTJ - 1) / kTJ, (a.Ly + kWarps * kRows - 1) / (kWarps * kRows));
+    const dim3 grid(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + kWarps * kRows - 1) / (kWarps * kRows)));
     sweep_kernel<S, F, E, kRows><<<grid, dim3(32, kWarps), 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -13,17 +13,19 @@ template <typename S, int R, bool MEASURE, int SAMPLE>
 __global__ void __launch_bounds__(256, 4) sweep_f32_kernel(const SweepArgs a)
 {
     __shared__ __align__(16) TileSmem<R> sm;
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
+    const int b = blockIdx.x;
+    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    sweep_tile<S, R, MEASURE, SAMPLE>(a, blockIdx.x, blockIdx.y, sm, eslot);
+    sweep_tile<S, R, MEASURE, SAMPLE>(a, b % ntx, b / ntx, sm, eslot);
 }
 
 template <typename S, bool MEASURE, int SAMPLE>
 cudaError_t go(const SweepArgs& a, cudaStream_t st)
 {
-    const dim3 grid((a.Lxh + kTJ - 1) / kTJ, (a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>());
+    const dim3 grid(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>()));
     sweep_f32_kernel<S, kRows, MEASURE, SAMPLE><<<grid, dim3(32, kWarps), 0, st>>>(a);
     return cudaGetLastError();
 }

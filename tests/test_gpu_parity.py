@@ -436,3 +436,31 @@ def test_single_sweep_other_q(mpr, orc, setup, q):
     assert np.all(d[~excused] <= tol + 2 * _ulp_store(setup)), d[~excused].max()
     assert excused.mean() < 0.01
     assert abs(e_s - o.energy_sample(phi, pr.mask)[0]) < 1e-12
+
+
+def test_tall_thin_grid_beyond_grid_limits(mpr, orc):
+    # more rows than a 2-D launch grid has in y (65535): init, sweeps, energy and prediction
+    Lx, Ly = 3, 70001
+    pr = mpr_inputs.make_problem(Lx, Ly, 0.5, field_seed=31, mask_seed=32, periodic=True)
+    for setup in ("DDD", "SDS"):
+        o, state = _start_state(orc, pr, setup, 2)
+        h = mpr.mpr_create(pr.z, pr.mask)
+        try:
+            mpr.mpr_set_options(h, setup, seed=2)
+            init, _ = mpr.mpr_get_state(h)
+            exp0 = _round_store(o.init(o.map(pr.z, pr.mask)[0], pr.mask), setup)
+            assert np.array_equal(init, exp0)
+            mpr.mpr_set_state(h, state, 0)
+            mpr.mpr_set_temperature(h, 0.5)
+            mpr.mpr_run(h, 0, 1)   # one sweep, sampled
+            got, _ = mpr.mpr_get_state(h)
+            zhat = mpr.mpr_predict(h)
+        finally:
+            mpr.mpr_destroy(h)
+        exp, mm, om = o.sweep(state, pr.mask, 0.5, 0, margins=True)
+        thr = 1e-11 if setup == "DDD" else 1e-4
+        bad = (mm < thr) | (om < thr)
+        col = _colour(Lx, Ly)
+        excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
+        assert np.all(np.abs(got - exp)[~excused] <= (1e-9 if setup == "DDD" else 1e-4))
+        assert np.array_equal(zhat[pr.mask == 1], pr.z[pr.mask == 1])
