@@ -168,13 +168,13 @@ class ClockSampler:
 def sweep_kernel_id() -> str:
     """Hash of the sweep kernel's sources: ties stored ncu counters to the code they came from."""
     h = hashlib.sha256()
-    for f in ("mpr_tile_f32.cuh", "mpr_sweep_f32.cu", "mpr_device.cuh"):
+    for f in ("mpr_tile_f32.cuh", "mpr_sweep_f32.cu", "mpr_device.cuh", "mpr_tma.cuh"):
         with open(os.path.join(ROOT, "paper_1910_08448_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel_id: str, workload: str):
+def stored_traffic(kernel_id: str, kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as fh:
@@ -182,9 +182,13 @@ def stored_traffic(kernel_id: str, workload: str):
     except (OSError, ValueError):
         return None
     e = d.get(workload)
-    if not e or e.get("kernel_id") != kernel_id:
+    if not e or e.get("kernel_id") != kernel_id or e.get("kernel") != kernel:
         return None
     return e.get("bytes_per_launch")
+
+
+# kernel that ran the plain passes, by mpr_info.sweep_kernel
+SWEEP_KERNELS = {-1: "mpr::sweep_kernel", 0: "mpr::sweep_f32_kernel", 1: "mpr::sweep_f32_tma_kernel"}
 
 
 def peaks():
@@ -271,8 +275,9 @@ def run_mine(args, dist: Dist):
     t_hbm = bytes_launch / (hbm_gbs * 1e9)
     t_mufu = mufu_launch / mufu_peak
     kid = sweep_kernel_id()
+    kname = SWEEP_KERNELS[infos[-1]["sweep_kernel"]]
     workload = f"L{L}_p{p}_{args.setup}"
-    traffic = stored_traffic(kid, workload)
+    traffic = stored_traffic(kid, kname, workload)
     if t_hbm >= t_mufu:
         roof = {"bound": "hbm", "achieved": bytes_launch / t_launch / 1e9, "peak": hbm_gbs,
                 "unit": "GB/s"}
@@ -280,7 +285,7 @@ def run_mine(args, dist: Dist):
         roof = {"bound": "alu", "achieved": mufu_launch / t_launch / 1e9,
                 "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof.update({"traffic": traffic, "peak_source": src, "kernel": "mpr::sweep_f32_kernel" if args.setup[2] == "S" else "mpr::sweep_kernel",
+    roof.update({"traffic": traffic, "peak_source": src, "kernel": kname,
                  "launch_us": t_launch * 1e6, "algorithmic_bytes_per_launch": bytes_launch,
                  "algorithmic_mufu_per_launch": mufu_launch, "kernel_id": kid,
                  "hbm_frac": bytes_launch / t_launch / 1e9 / hbm_gbs,

@@ -93,6 +93,8 @@ typedef struct {
     uint64_t kernel_launches;  /* kernels launched by the handle since creation               */
     double prof_sweep_ms;      /* with profiling on: device time of the pure sweep segments   */
     uint64_t prof_sweep_launches; /* ... and the number of sweep-kernel launches they hold    */
+    int sweep_kernel;          /* FP32-function sweeps: 0 = one tile per block, 1 = TMA-fed   */
+                               /* persistent kernel; -1 = not chosen yet, or FP64 functions   */
 } mpr_info;
 
 /* mpr_create: copies the host grid (values: Lx*Ly doubles, ignored where mask == 0 and may be
@@ -142,6 +144,18 @@ mpr_status mpr_get_info(mpr_handle h, mpr_info* info);
 /* on != 0: bracket every run of sweeps without energy or sample work (equilibration) with CUDA
  * events on the handle's stream and accumulate their device time into prof_sweep_ms. */
 mpr_status mpr_set_profiling(mpr_handle h, int on);
+
+/* Sweep kernel of the FP32-function setups; both compute identical states, bit for bit.
+ * kind 0: one tile (128 half-lattice columns x 16 rows) per block, staged with ordinary loads.
+ * kind 1: persistent blocks over 128 x 32 tiles; the TMA unit copies the next tile's boxes into
+ *         shared memory (cp.async.bulk.tensor, mbarrier with a bounded wait) while the block
+ *         updates the current one. Needs a lattice at least two tiles wide (Lx > 256) and 34 rows.
+ * kind -1 (default): automatic. The first run of at least 12 sweeps without energy or sample
+ *         work (an equilibration, or a tuning probe's) times 5 sweeps of each kernel after one
+ *         warm-up sweep each, as ordinary sweeps of the chain, and keeps the faster.
+ * INVALID_ARG if kind is not -1, 0 or 1, or kind 1 is unavailable for the handle. A forced kind
+ * stays across mpr_set_options while it remains available; an automatic choice is redone. */
+mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind);
 
 /* State access for checkpoints and tests: angles as Lx*Ly doubles, row-major, host memory.
  * mpr_set_state writes the prediction sites only (rounded to the storage type), leaves the

@@ -59,7 +59,8 @@ class mpr_info(ctypes.Structure):
                 ("sweep", ctypes.c_uint32), ("n_samples", ctypes.c_int), ("n_probes", ctypes.c_int),
                 ("e_bond_mean", ctypes.c_double), ("site_updates", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_uint64),
-                ("prof_sweep_ms", ctypes.c_double), ("prof_sweep_launches", ctypes.c_uint64)]
+                ("prof_sweep_ms", ctypes.c_double), ("prof_sweep_launches", ctypes.c_uint64),
+                ("sweep_kernel", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -94,6 +95,7 @@ def load():
             "mpr_energy": ([H, P(d), P(d)], i),
             "mpr_get_info": ([H, P(mpr_info)], i),
             "mpr_set_profiling": ([H, i], i),
+            "mpr_set_sweep_kernel": ([H, i], i),
             "mpr_get_state": ([H, vp, P(u32)], i),
             "mpr_set_state": ([H, vp, u32], i),
             "mpr_philox4x32_10_dev": ([vp, vp, i, u64, vp], i),
@@ -127,6 +129,7 @@ def exported_symbols():
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_run", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
+            "mpr_set_sweep_kernel",
             "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error",
             "mpr_batch_create", "mpr_batch_destroy", "mpr_batch_set_stream",
             "mpr_batch_set_tuning", "mpr_batch_set_launch", "mpr_batch_autotune",
@@ -263,6 +266,11 @@ def mpr_get_info(h) -> dict:
 
 def mpr_set_profiling(h, on: bool = True):
     _check(load().mpr_set_profiling(h, int(bool(on))))
+
+
+def mpr_set_sweep_kernel(h, kind: int):
+    """FP32-function sweep kernel: -1 automatic (default), 0 one tile per block, 1 TMA-fed."""
+    _check(load().mpr_set_sweep_kernel(h, int(kind)))
 
 
 def mpr_get_state(h):

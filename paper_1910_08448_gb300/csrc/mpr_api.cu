@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -118,7 +119,20 @@ struct mpr_ctx {
     int eseries_cap = 0;
     double* tmpN = nullptr;              // N doubles for state transfer / prediction
     double* host = nullptr;              // pinned host staging (16 doubles)
+
+    // TMA descriptors of the half-lattices (FP32-function sweeps of lattices wider than a tile)
+    TmaMaps tma{};
+    int nsm = 0;                         // SMs of the device
+    int sweep_force = -1;                // mpr_set_sweep_kernel: -1 automatic, 0, 1
+    int sweep_kind = -1;                 // automatic choice (-1 until made)
+    cudaEvent_t cal[4] = {nullptr, nullptr, nullptr, nullptr};   // timing of the choice
 };
+
+constexpr int kCalSweeps = 5;            // timed sweeps per kernel in the automatic choice
+
+// Device error word of the handle: the last of the 16 device scalars (zeroed at creation).
+inline int* dev_err(mpr_ctx* h) { return reinterpret_cast<int*>(h->scal + 15); }
+inline int* host_err(mpr_ctx* h) { return reinterpret_cast<int*>(h->host + 15); }
 
 namespace {
 
@@ -178,6 +192,10 @@ void free_all(mpr_ctx* h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     h->ev0 = h->ev1 = nullptr;
+    for (cudaEvent_t& e : h->cal) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
 }
 
 mpr_status harvest_profile(mpr_ctx* h)
@@ -192,9 +210,20 @@ mpr_status harvest_profile(mpr_ctx* h)
     return MPR_OK;
 }
 
+// Waits for the handle's stream; reports a device-side wait that ran out (MPR_ERR_DEVICE_TIMEOUT)
+// since the previous check, then clears the error word.
 mpr_status sync(mpr_ctx* h)
 {
+    CU(cudaMemcpyAsync(host_err(h), dev_err(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    if (*host_err(h) != 0) {
+        const int e = *host_err(h);
+        *host_err(h) = 0;
+        CU(cudaMemsetAsync(dev_err(h), 0, sizeof(int), h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return fail(e == MPR_ERR_DEVICE_TIMEOUT ? MPR_ERR_DEVICE_TIMEOUT : MPR_ERR_CUDA,
+                    "a device-side wait for a TMA copy ran out");
+    }
     return harvest_profile(h);
 }
 
@@ -228,6 +257,11 @@ mpr_status init_state(mpr_ctx* h)
             CU(cudaMemsetAsync(h->acc_lo[c], 0, accf_bytes(h), h->stream));
         }
     }
+    // TMA maps for the FP32-function kernel (false: the lattice is too narrow for its boxes)
+    h->tma = TmaMaps{};
+    if (p.func == 1) make_sweep_maps(h->L, p.store, h->ang, h->mb, &h->tma);
+    h->sweep_kind = -1;   // the storage type may have changed: choose again
+    if (h->sweep_force == 1 && !h->tma.ok) h->sweep_force = -1;
     CU(launch_init(h->L, p, h->z, h->mask, h->scal, h->ang[0], h->ang[1], h->mb[0], h->mb[1],
                    h->opt.seed, 0u, h->stream));
     h->launches += 3;   // init + sample energy (2)
@@ -286,7 +320,7 @@ mpr_status create_common(int Lx, int Ly, const double* values, const unsigned ch
     const int nmm = 256;
     {
         const int sb = sweep_blocks(h->L, h->prec), sf = sweep_f32_blocks(h->L);
-        size_t need = (size_t)(sb > sf ? sb : sf) * 8;
+        size_t need = (size_t)std::max(sb, sf) * 8;
         size_t a = (size_t)sample_energy_blocks(h->L) * 16;
         size_t b = (size_t)energy_blocks(h->L) * 8;
         size_t c = (size_t)nmm * 32;
@@ -295,6 +329,10 @@ mpr_status create_common(int Lx, int Ly, const double* values, const unsigned ch
     }
     if ((s = dalloc(h, &h->part, h->part_bytes)) != MPR_OK) return bail(s);
     if ((s = dalloc(h, &h->scal, 16 * 8)) != MPR_OK) return bail(s);
+    if (cudaMemsetAsync(h->scal, 0, 16 * 8, stream) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return bail(fail(MPR_ERR_CUDA, "device query failed"));
+    h->host[15] = 0.0;
     if ((s = dalloc(h, &h->z, (size_t)h->N * 8)) != MPR_OK) return bail(s);
     if ((s = dalloc(h, &h->mask, (size_t)h->N)) != MPR_OK) return bail(s);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -329,7 +367,13 @@ mpr_status ensure_eseries(mpr_ctx* h, int n)
 }
 
 // n hybrid sweeps at temperature T; with kMeasure the raw bond sum of sweep k lands in
-// eseries[k]. Every launch goes to the handle's stream; nothing here synchronises.
+// eseries[k]. Every launch goes to the handle's stream; nothing here synchronises, except the
+// one-time choice of the FP32 sweep kernel (sweep_kind), which waits for its timing events.
+//
+// Kernel choice: the TMA kernel (kind 1) and the one-tile-per-block kernel (kind 0) change the
+// state identically, but their energy partials come from tiles of different heights, so passes
+// with the fused energy (kMeasure) always run kind 0: energies stay bit-identical whatever kind
+// the plain passes use.
 mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
 {
     if (n <= 0) return MPR_OK;
@@ -350,6 +394,8 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.qf = (float)h->opt.q;
     a.invTf = (float)(1.0 / T);
     a.epart = h->part;
+    a.err = dev_err(h);
+    a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds
     const bool f32 = h->prec.func == 1;
     const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);
     const bool timed = h->prof && flags == 0;
@@ -357,23 +403,49 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
         CHECK(harvest_profile(h));
         CU(cudaEventRecord(h->ev0, h->stream));
     }
-    for (int k = 0; k < n; ++k) {
+    // one hybrid sweep (both colour passes) with kernel kind (0/1; ignored for FP64 functions)
+    auto one = [&](int k, int kind) -> mpr_status {
         a.sweep = h->sweep;
         for (int c = 0; c < 2; ++c) {
             a.colour = c;
+            a.ph = philox_sched(a.sweep, a.problem, kTagMetropolis, (uint32_t)c, a.seed_lo, a.seed_hi);
             a.own = h->ang[c];
             a.other = h->ang[c ^ 1];
             a.mbits = h->mb[c];
             a.acc = h->acc[c];
             a.acc_hi = h->acc_hi[c];
             a.acc_lo = h->acc_lo[c];
-            CU(f32 ? launch_sweep_f32(h->prec, a, h->stream) : launch_sweep(h->prec, a, h->stream));
+            CU(!f32 ? launch_sweep(h->prec, a, h->stream)
+                    : kind == 1 ? launch_sweep_f32_tma(h->prec, a, h->tma, h->nsm, h->stream)
+                                : launch_sweep_f32(h->prec, a, h->stream));
         }
         if (flags & kMeasure) CU(launch_reduce(h->prec, h->part, nblk, h->eseries + k, h->stream));
         h->launches += (flags & kMeasure) ? 3 : 2;
         ++h->sweep;
         h->site_updates += (uint64_t)h->Np;
+        return MPR_OK;
+    };
+    const bool tma_ok = f32 && h->tma.ok && !(flags & kMeasure);
+    int k = 0;
+    if (tma_ok && h->sweep_force < 0 && h->sweep_kind < 0 && flags == 0 && n >= 2 * (1 + kCalSweeps)) {
+        // automatic choice: one warm-up and kCalSweeps timed sweeps of each kernel, as ordinary
+        // sweeps of the chain (both kernels give the same states), then the faster one
+        if (!h->cal[0])
+            for (cudaEvent_t& e : h->cal) CU(cudaEventCreate(&e));
+        float ms[2] = {0.f, 0.f};
+        for (int kind = 0; kind < 2; ++kind) {
+            CHECK(one(k++, kind));
+            CU(cudaEventRecord(h->cal[2 * kind], h->stream));
+            for (int i = 0; i < kCalSweeps; ++i) CHECK(one(k++, kind));
+            CU(cudaEventRecord(h->cal[2 * kind + 1], h->stream));
+        }
+        CU(cudaEventSynchronize(h->cal[3]));
+        for (int kind = 0; kind < 2; ++kind)
+            CU(cudaEventElapsedTime(&ms[kind], h->cal[2 * kind], h->cal[2 * kind + 1]));
+        h->sweep_kind = ms[1] < ms[0] ? 1 : 0;
     }
+    const int kind = !tma_ok ? 0 : h->sweep_force >= 0 ? h->sweep_force : (h->sweep_kind > 0 ? 1 : 0);
+    for (; k < n; ++k) CHECK(one(k, kind));
     if (timed) {
         CU(cudaEventRecord(h->ev1, h->stream));
         h->prof_pending = true;
@@ -602,6 +674,20 @@ mpr_status mpr_get_info(mpr_handle h, mpr_info* info)
     info->kernel_launches = h->launches;
     info->prof_sweep_ms = h->prof_ms;
     info->prof_sweep_launches = h->prof_launches;
+    info->sweep_kernel = h->prec.func == 0 ? -1
+                         : !h->tma.ok ? 0
+                         : h->sweep_force >= 0 ? h->sweep_force : h->sweep_kind;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (kind < -1 || kind > 1) return fail(MPR_ERR_INVALID_ARG, "sweep kernel %d: use -1, 0 or 1", kind);
+    if (kind == 1 && !(h->prec.func == 1 && h->tma.ok))
+        return fail(MPR_ERR_INVALID_ARG,
+                    "the TMA sweep kernel needs FP32 functions and a lattice of Lx > 256, Ly >= 34");
+    h->sweep_force = kind;
     return MPR_OK;
 }
 

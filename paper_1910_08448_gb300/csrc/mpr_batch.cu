@@ -249,7 +249,7 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
     a.invTf = __ldcg(&P.d.invTf);
     const int i = t - P.tile_base;
     void* eslot = MEASURE ? static_cast<char*>(A->epart) + (size_t)t * (A->energy_f32 ? 4 : 8) : nullptr;
-    sweep_tile<S, R, MEASURE, SAMPLE>(a, i % P.ntx, i / P.ntx, *reinterpret_cast<TileSmem<R>*>(dsm),
+    sweep_tile<S, R, MEASURE, SAMPLE, false>(a, i % P.ntx, i / P.ntx, *reinterpret_cast<TileSmem<R>*>(dsm),
                                       eslot);
 }
 

@@ -711,6 +711,7 @@ mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info)
     info->site_updates = p.d.site_updates;
     info->device_bytes = b->bytes;
     info->kernel_launches = b->launches;
+    info->sweep_kernel = 0;   // batch tiles are staged with ordinary loads
     return MPR_OK;
 }
 

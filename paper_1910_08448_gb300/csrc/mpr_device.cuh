@@ -47,13 +47,59 @@ __device__ __forceinline__ uint4 pair_words(uint32_t jpair, uint32_t y, uint32_t
                          seed_lo, seed_hi);
 }
 
+// The same words with the work that is constant over one colour pass done once, on the host or
+// once per tile: the ten round keys, and the half of round 1 that depends only on the counter's
+// sweep and tag words (they multiply and mix the same way for every site of the pass). Round keys
+// then enter the mixing straight from kernel parameters.
+struct PhiloxSched {
+    uint32_t a, b, c;   // round 1: hi(M1 * sweep) ^ k0, lo(M1 * sweep), ctr.w ^ k1
+    uint32_t k[18];     // keys of rounds 2 .. 10: (k0, k1) pairs
+};
+
+__host__ __device__ inline PhiloxSched philox_sched(uint32_t sweep, uint32_t problem, uint32_t tag,
+                                                    uint32_t colour, uint32_t seed_lo,
+                                                    uint32_t seed_hi)
+{
+    PhiloxSched s;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * sweep;
+    s.a = (uint32_t)(p1 >> 32) ^ seed_lo;
+    s.b = (uint32_t)p1;
+    s.c = ((problem << 8) | (tag << 1) | colour) ^ seed_hi;
+    uint32_t k0 = seed_lo, k1 = seed_hi;
+    for (int r = 1; r < 10; ++r) {
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        s.k[2 * (r - 1)] = k0;
+        s.k[2 * (r - 1) + 1] = k1;
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint4 pair_words(uint32_t jpair, uint32_t y, const PhiloxSched& s)
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * jpair;
+    uint4 x = make_uint4(s.a ^ y, s.b, (uint32_t)(p0 >> 32) ^ s.c, (uint32_t)p0);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint64_t q0 = (uint64_t)0xD2511F53u * x.x;
+        const uint64_t q1 = (uint64_t)0xCD9E8D57u * x.z;
+        x = make_uint4((uint32_t)(q1 >> 32) ^ x.y ^ s.k[2 * (r - 1)], (uint32_t)q1,
+                       (uint32_t)(q0 >> 32) ^ x.w ^ s.k[2 * (r - 1) + 1], (uint32_t)q0);
+    }
+    return x;
+}
+
 // Uniforms in [0, 1): FP64 functions take all 32 bits, FP32 functions the top 23 bits.
 __device__ __forceinline__ double uniform_d(uint32_t w) { return (double)w * 2.3283064365386962890625e-10; }
-__device__ __forceinline__ float uniform_f(uint32_t w)
+// 1 + uniform_f(w), exactly: 1.m with the top 23 bits of w as mantissa (the exponent bits of 1.0
+// are added: the shifted word has none, so the sum equals the bitwise or, in one shift-add).
+__device__ __forceinline__ float one_plus_uniform_f(uint32_t w)
 {
-    // 1.m with the top 23 bits as mantissa, minus 1: exactly (w >> 9) * 2^-23, no conversion op.
-    return __uint_as_float(0x3f800000u | (w >> 9)) - 1.0f;
+    return __uint_as_float((w >> 9) + 0x3f800000u);
 }
+// Exactly (w >> 9) * 2^-23, no conversion op. c * uniform_f(w) == fmaf(c, one_plus_uniform_f(w), -c)
+// bit for bit, since both round the same exact product once.
+__device__ __forceinline__ float uniform_f(uint32_t w) { return one_plus_uniform_f(w) - 1.0f; }
 
 // ---------------------------------------------------------------------------------------------
 // Storage conversions

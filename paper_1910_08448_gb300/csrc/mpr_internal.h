@@ -2,10 +2,13 @@
 // launchers and the layout they share). Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
+
+#include "mpr_device.cuh"   // PhiloxSched
 
 namespace mpr {
 
@@ -56,6 +59,18 @@ struct SweepArgs {
     uint32_t seed_lo, seed_hi, sweep, problem;
     double q, T, invT;
     float qf, invTf;           // the same in FP32 for the FP32-function kernel (no FP64 on device)
+    int* err;                  // device error word (MPR_ERR_DEVICE_TIMEOUT) or NULL
+    long long wait_ns;         // limit of one device-side wait (TMA kernel)
+    PhiloxSched ph;            // Philox schedule of this pass (FP32-function single-problem kernels)
+};
+
+// TMA descriptors of one problem's half-lattices for the TMA-fed FP32 sweep kernel: per colour c
+// the staging box of the other-colour role, the own-values box and the mask-word box.
+struct TmaMaps {
+    CUtensorMap other[2];
+    CUtensorMap own[2];
+    CUtensorMap mask[2];
+    bool ok = false;
 };
 
 // Launchers (all asynchronous on `st`); each returns the launch's cudaError_t.
@@ -64,6 +79,13 @@ int sweep_blocks(const Layout& L, const Precision& p);
 cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st);
 int sweep_f32_blocks(const Layout& L);
 cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st);
+// TMA kernel: maps for the layout and storage (false when the lattice is too small for its boxes,
+// or the driver has no tensor maps; the one-tile-per-block kernel then runs); the launch of a
+// plain pass (no kMeasure, no kSample) on nsm SMs.
+bool make_sweep_maps(const Layout& L, int store, void* const ang[2], uint32_t* const mb[2],
+                     TmaMaps* out);
+cudaError_t launch_sweep_f32_tma(const Precision& p, const SweepArgs& a, const TmaMaps& m, int nsm,
+                                 cudaStream_t st);
 
 cudaError_t launch_minmax(const double* z, const unsigned char* mask, long long N, double* part,
                           int nblk, double* out4, cudaStream_t st);

@@ -19,28 +19,33 @@ namespace f32 {
 constexpr int kTJ = 128;     // half-lattice columns per tile
 constexpr int kWarps = 8;    // 256 threads, blockDim = (32, 8)
 
-// atan2 in FP32: reduce to a = min(|x|,|y|)/max(|x|,|y|) in [0, 1], evaluate atan(a) = a*P(a^2),
-// then map the octant back. P is a degree-7 polynomial in a^2 fitted for this library by Lawson's
-// iteratively reweighted least squares (a minimax method) to atan on [0, 1]: max error 3.8e-8 rad,
-// below the FP32 spacing of angles near pi/4. The quotient uses the approximate FP32 division.
-__device__ __forceinline__ float atan2_fast(float y, float x)
+// Twice atan2(y, x) modulo 2*pi, in FP32, as an angle in [-pi, pi] (the over-relaxation needs the
+// doubled angle only modulo 2*pi). Reduce to a = min(|x|,|y|)/max(|x|,|y|) in [0, 1] and evaluate
+// 2 atan(a) = a*P(a^2); P is a degree-7 polynomial in a^2 fitted for this library by Lawson's
+// iteratively reweighted least squares (a minimax method) to atan on [0, 1], max error 3.8e-8
+// rad, here with every coefficient doubled (exact: Horner's rounding commutes with the factor 2).
+// In the first quadrant the doubled angle is 2t (|y| <= |x|) or pi - 2t; reflecting into the other
+// quadrants maps it to its negative modulo 2 pi (x < 0: 2(pi - t1) = -2 t1; y < 0: -2 t1), so the
+// sign of the result is the sign of x*y, applied by flipping the sign bit. The quotient uses the
+// approximate FP32 division; x = y = 0 gives NaN.
+__device__ __forceinline__ float atan2_doubled(float y, float x)
 {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
     const float a = __fdividef(mn, mx);
     const float s = a * a;
-    float p = -0.004054565913975239f;
-    p = fmaf(p, s, 0.021862953901290894f);
-    p = fmaf(p, s, -0.0559123195707798f);
-    p = fmaf(p, s, 0.0964219719171524f);
-    p = fmaf(p, s, -0.1390862911939621f);
-    p = fmaf(p, s, 0.19946566224098206f);
-    p = fmaf(p, s, -0.33329859375953674f);
-    p = fmaf(p, s, 0.9999993443489075f);
-    float t = a * p;
-    t = (ay > ax) ? 1.57079632679489662f - t : t;
-    t = (x < 0.0f) ? 3.14159265358979324f - t : t;
-    return (y < 0.0f) ? -t : t;
+    float p = -0.008109131827950478f;
+    p = fmaf(p, s, 0.04372590780258179f);
+    p = fmaf(p, s, -0.1118246391415596f);
+    p = fmaf(p, s, 0.1928439438343048f);
+    p = fmaf(p, s, -0.2781725823879242f);
+    p = fmaf(p, s, 0.3989313244819641f);
+    p = fmaf(p, s, -0.6665971875190735f);
+    p = fmaf(p, s, 1.999998688697815f);
+    float t2 = a * p;
+    t2 = (ay > ax) ? 3.14159265358979324f - t2 : t2;
+    const uint32_t sgn = (__float_as_uint(x) ^ __float_as_uint(y)) & 0x80000000u;
+    return __uint_as_float(__float_as_uint(t2) ^ sgn);
 }
 
 template <typename S> struct Raw4;
@@ -100,9 +105,40 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile as unit vectors
-// (cos q*phi, sin q*phi); entries outside the lattice are (0, 0) (open boundaries). All loads are
-// issued before the sin/cos work. CHECK = false when the caller knows every entry exists.
+// Converts one staged row r (tile row y = y0 - 1 + r, parity ob of its columns) of the other
+// colour to unit vectors (cos q*phi, sin q*phi) in sm: the thread's four columns from st, the halo
+// column j0 - 1 (lane 0) or j0 + TJ (lane 1) from halo. Entries outside the lattice become (0, 0)
+// (open boundaries); CHECK = false when the caller knows every entry exists.
+template <typename S, int R, bool CHECK>
+__device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j0, int jb, int lj,
+                                         int ob, float q, const Pack4<S>& st, S halo,
+                                         TileSmem<R>& sm)
+{
+    const int lane = threadIdx.x;
+    const bool row_ok = !CHECK || (y >= 0 && y < a.Ly);
+    float vc[4], vs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        vc[k] = 0.0f;
+        vs[k] = 0.0f;
+        if (!CHECK || (row_ok && 2 * (jb + k) + ob < a.Lx))
+            __sincosf(q * load_as<float>(st.s[k]), &vs[k], &vc[k]);
+    }
+    *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
+    *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
+        const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
+        const int cc = lane == 0 ? 3 : kTJ + 4;
+        float hc = 0.0f, hs = 0.0f;
+        if (!CHECK || (row_ok && j >= 0 && 2 * j + ob < a.Lx))
+            __sincosf(q * load_as<float>(halo), &hs, &hc);
+        sm.cs[r][cc] = hc;
+        sm.sn[r][cc] = hs;
+    }
+}
+
+// Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile from global
+// memory as unit vectors. All loads are issued before the sin/cos work.
 template <typename S, int R, bool CHECK>
 __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ other, int y0,
                                       int j0, int jb, int lj, int cb, float q, TileSmem<R>& sm)
@@ -130,98 +166,58 @@ __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ 
         const int r = warp + i * kWarps;
         if (r >= TY + 2) break;
         const int y = y0 - 1 + r;
-        const bool row_ok = !CHECK || (y >= 0 && y < a.Ly);
-        const int ob = (y + cb) & 1;
-        float vc[4], vs[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            vc[k] = 0.0f;
-            vs[k] = 0.0f;
-            if (!CHECK || (row_ok && 2 * (jb + k) + ob < a.Lx))
-                __sincosf(q * load_as<float>(st[i].s[k]), &vs[k], &vc[k]);
-        }
-        *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
-        *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
-            const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
-            const int cc = lane == 0 ? 3 : kTJ + 4;
-            float hc = 0.0f, hs = 0.0f;
-            if (!CHECK || (row_ok && j >= 0 && 2 * j + ob < a.Lx))
-                __sincosf(q * load_as<float>(halo[i]), &hs, &hc);
-            sm.cs[r][cc] = hc;
-            sm.sn[r][cc] = hs;
-        }
+        unit_row<S, R, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st[i], halo[i], sm);
     }
 }
 
-// One tile (tile column tx, tile row ty) of colour a.colour. SAMPLE: 0 none, 1 FP64 accumulators,
-// 2 Kahan FP32 accumulators. With MEASURE (black pass) the tile's sum of u_b . h_b over its
-// existing black sites is written by thread (0, 0) to *eslot (double, or float with kEnergyF32).
-// Begins with a block barrier, so a block may call it for several tiles in a row.
-template <typename S, int R, bool MEASURE, int SAMPLE>
-__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R>& sm,
-                                           void* eslot)
+// Two FP32 results rounded to a 16-bit storage type by one paired conversion (each half rounds
+// exactly as a single conversion would), packed low = a, high = b.
+template <typename S> __device__ __forceinline__ uint32_t pack2(float a, float b);
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float a, float b)
 {
-    constexpr int TY = kWarps * R;
-    const int c = a.colour, cb = c ^ 1;
-    const int j0 = tx * kTJ;
-    const int y0 = ty * TY;
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    const S* __restrict__ other = static_cast<const S*>(a.other);
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Metropolis + over-relaxation of the thread's four columns jb .. jb+3 of tile row ly (lattice
+// row y < Ly) of colour a.colour, reading the staged neighbours in sm; pk holds the four stored
+// values (updated in place and written back as one vector), bits their frozen bits. SAMPLE: 0
+// none, 1 FP64 accumulators, 2 Kahan FP32 accumulators. MEASURE adds u_b . h_b of the row's
+// existing (black) sites to e_d or e_f. SCHED: Philox words from the precomputed schedule a.ph
+// (a kernel parameter) instead of the seed. OPAR: the row's column offset o = (y + colour) & 1
+// when the caller knows it at compile time (0 or 1), else -1.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR>
+__device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
+                                           Pack4<S>& pk, uint32_t bits, const TileSmem<R>& sm,
+                                           double& e_d, float& e_f)
+{
+    const int c = a.colour;
     S* __restrict__ own = static_cast<S*>(a.own);
     const float q = a.qf;
-    const int jb = j0 + 4 * lane;             // first of this thread's 4 columns
-    const int lj = 4 * lane;
-
-    // ---- own rows: values and frozen bits, loaded before the staging so their latency overlaps
-    Pack4<S> mine[R];
-    uint32_t bits[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int y = y0 + warp * R + rr;
-        bits[rr] = 0xFu;
-        if (y < a.Ly) {
-            load4(own + (size_t)y * a.pitch + jb, mine[rr]);
-            bits[rr] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
-        }
-    }
-
-    __syncthreads();   // the previous tile's readers are done with sm
-    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
-    // lies inside the lattice (nearly all) skip the per-entry bounds checks.
-    const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
-    if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, q, sm);
-    else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, q, sm);
-    __syncthreads();
-
     const float nl2e_invT = -1.4426950408889634f * a.invTf;   // exp(-dE/T) = 2^(dE * nl2e_invT)
     const float two_pi = kTwoPiF;
     const float width = two_pi * q;
     const float inv_q = 1.0f / q;
-    double e_d = 0.0;
-    float e_f = 0.0f;
-
+    const int o = OPAR >= 0 ? OPAR : ((y + c) & 1);
+    const size_t idx = (size_t)y * a.pitch + jb;
+    // entries past the row's end carry frozen bits (padding), so the bit alone decides an update;
+    // existence matters only for the energy sum
+    bool ex[4], upd[4];
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int ly = warp * R + rr;
-        const int y = y0 + ly;
-        if (y >= a.Ly) break;
-        const int o = (y + c) & 1;
-        const size_t idx = (size_t)y * a.pitch + jb;
-        bool ex[4], upd[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            ex[k] = 2 * (jb + k) + o < a.Lx;
-            upd[k] = ex[k] && !((bits[rr] >> k) & 1u);
-        }
-        Pack4<S>& pk = mine[rr];
-        // both Philox calls of the row, whether or not their sites update: no branch per site
-        uint4 w[2];
-#pragma unroll
-        for (int pr = 0; pr < 2; ++pr)
-            w[pr] = pair_words((uint32_t)((jb >> 1) + pr), (uint32_t)y, a.sweep, a.problem,
-                               kTagMetropolis, (uint32_t)c, a.seed_lo, a.seed_hi);
-        // neighbours: up/down rows at the same columns, the middle row at columns j+o-1, j+o
+    for (int k = 0; k < 4; ++k) {
+        ex[k] = 2 * (jb + k) + o < a.Lx;
+        upd[k] = !((bits >> k) & 1u);
+    }
+    // local fields h = sum of the neighbours' unit vectors (left, right, up, down), all four sites
+    // first: the neighbour vectors are dead before the moves start
+    float hx[4], hy[4];
+    {
+        // up/down rows at the same columns, the middle row at columns j+o-1, j+o
         const float4 uc = *reinterpret_cast<const float4*>(&sm.cs[ly][4 + lj]);
         const float4 us = *reinterpret_cast<const float4*>(&sm.sn[ly][4 + lj]);
         const float4 dc = *reinterpret_cast<const float4*>(&sm.cs[ly + 2][4 + lj]);
@@ -237,81 +233,185 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const float dcv[4] = {dc.x, dc.y, dc.z, dc.w}, dsv[4] = {ds.x, ds.y, ds.z, ds.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            // local field h = sum of the neighbours' unit vectors (left, right, up, down)
-            const float hx = ((mcv[k] + mcv[k + 1]) + ucv[k]) + dcv[k];
-            const float hy = ((msv[k] + msv[k + 1]) + usv[k]) + dsv[k];
-            float f = load_as<float>(pk.s[k]);
-            {
-                // every site runs the move; frozen sites and padding discard the result below
-                const uint32_t wp = (k & 1) ? w[k >> 1].z : w[k >> 1].x;
-                const uint32_t wa = (k & 1) ? w[k >> 1].w : w[k >> 1].y;
-                const float u_prop = uniform_f(wp), u_acc = uniform_f(wa);
-                // Metropolis: uniform proposal, accept if dE <= 0 or u < exp(-dE/T)
-                const float fp = two_pi * u_prop;
-                float s0, c0, sp, cp;
-                __sincosf(q * f, &s0, &c0);
-                __sincosf(q * fp, &sp, &cp);
-                // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
-                const float dE = hx * (c0 - cp) + hy * (s0 - sp);
-                const bool accept = dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT);
-                const float f1 = accept ? fp : f;
-                // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
-                // h = 0 gives 0/0 = NaN in atan2_fast, every comparison below is false and the
-                // angle stays, as the move requires.
-                float r = 2.0f * atan2_fast(hy, hx) - q * f1;   // in [-2pi(1+q), 2pi]
-                r = r < 0.0f ? r + two_pi : r;
-                r = r < 0.0f ? r + two_pi : r;
-                const float fn = r <= width ? r * inv_q : f1;
+            hx[k] = ((mcv[k] + mcv[k + 1]) + ucv[k]) + dcv[k];
+            hy[k] = ((msv[k] + msv[k + 1]) + usv[k]) + dsv[k];
+        }
+    }
+    uint4 w;
+    float fn_even = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        // one Philox call per site pair, whether or not its sites update: no branch per site
+        if ((k & 1) == 0) {
+            const uint32_t jpair = (uint32_t)((jb >> 1) + (k >> 1));
+            if constexpr (SCHED)
+                w = pair_words(jpair, (uint32_t)y, a.ph);
+            else
+                w = pair_words(jpair, (uint32_t)y, a.sweep, a.problem, kTagMetropolis,
+                               (uint32_t)c, a.seed_lo, a.seed_hi);
+        }
+        const float hxk = hx[k], hyk = hy[k];
+        float f = load_as<float>(pk.s[k]);
+        {
+            // every site runs the move; frozen sites and padding discard the result below
+            const uint32_t wp = (k & 1) ? w.z : w.x;
+            const uint32_t wa = (k & 1) ? w.w : w.y;
+            const float u_acc = uniform_f(wa);
+            // Metropolis: uniform proposal fp = 2 pi u, accept if dE <= 0 or u_acc < exp(-dE/T)
+            const float fp = fmaf(two_pi, one_plus_uniform_f(wp), -two_pi);
+            float s0, c0, sp, cp;
+            __sincosf(q * f, &s0, &c0);
+            __sincosf(q * fp, &sp, &cp);
+            // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
+            const float dE = hxk * (c0 - cp) + hyk * (s0 - sp);
+            const bool accept = dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT);
+            const float f1 = accept ? fp : f;
+            // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
+            // h = 0 gives NaN in atan2_doubled, every comparison below is false and the angle
+            // stays, as the move requires.
+            float r = atan2_doubled(hyk, hxk) - q * f1;   // in [-pi - 2 pi q, pi]
+            r = r < 0.0f ? r + two_pi : r;
+            r = r < 0.0f ? r + two_pi : r;
+            const float fn = r <= width ? r * inv_q : f1;
+            if constexpr (sizeof(S) == 2) {
+                // 16-bit storage: the pair's two results rounded by one conversion and merged into
+                // the pair's 32-bit word under the update mask
+                if ((k & 1) == 0) {
+                    fn_even = fn;
+                } else {
+                    const uint32_t m = (upd[k - 1] ? 0x0000FFFFu : 0u) | (upd[k] ? 0xFFFF0000u : 0u);
+                    const uint32_t packed = pack2<S>(fn_even, fn);
+                    if (k == 1) pk.v.x = (packed & m) | (pk.v.x & ~m);
+                    else pk.v.y = (packed & m) | (pk.v.y & ~m);
+                }
+                if (SAMPLE || MEASURE) f = upd[k] ? load_as<float>(store_from<S>(fn)) : f;
+            } else {
                 const S stored = store_from<S>(fn);
                 pk.s[k] = upd[k] ? stored : pk.s[k];
                 f = upd[k] ? load_as<float>(stored) : f;
             }
-            if (SAMPLE == 1) {
-                if (upd[k]) a.acc[idx + k] += (double)f;
-            } else if (SAMPLE == 2) {
-                if (upd[k]) {
-                    // Kahan: hi carries the sum, lo the (negated) lost low-order part
-                    const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
-                    const float yv = f - lo;
-                    const float tt = hi + yv;
-                    a.acc_lo[idx + k] = (tt - hi) - yv;
-                    a.acc_hi[idx + k] = tt;
-                }
-            }
-            if (MEASURE && ex[k]) {
-                // every bond joins a red and a black site: sum over black sites of u_b . h_b
-                float sn, cs;
-                __sincosf(q * f, &sn, &cs);
-                const float e = cs * hx + sn * hy;
-                if (a.flags & kEnergyF32) e_f += e; else e_d += (double)e;
+        }
+        if (SAMPLE == 1) {
+            if (upd[k]) a.acc[idx + k] += (double)f;
+        } else if (SAMPLE == 2) {
+            if (upd[k]) {
+                // Kahan: hi carries the sum, lo the (negated) lost low-order part
+                const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
+                const float yv = f - lo;
+                const float tt = hi + yv;
+                a.acc_lo[idx + k] = (tt - hi) - yv;
+                a.acc_hi[idx + k] = tt;
             }
         }
-        store4(own + idx, pk);   // unchanged entries are written back with their own bits
+        if (MEASURE && ex[k]) {
+            // every bond joins a red and a black site: sum over black sites of u_b . h_b
+            float sn, cs;
+            __sincosf(q * f, &sn, &cs);
+            const float e = cs * hxk + sn * hyk;
+            if (a.flags & kEnergyF32) e_f += e; else e_d += (double)e;
+        }
+    }
+    store4(own + idx, pk);   // unchanged entries are written back with their own bits
+}
+
+// The tile's energy partial: warp shuffles, then the warps in order, written by thread (0, 0) to
+// *eslot (double, or float with kEnergyF32). Contains a block barrier.
+template <int R>
+__device__ __forceinline__ void tile_energy(const SweepArgs& a, double e_d, float e_f,
+                                            TileSmem<R>& sm, void* eslot)
+{
+    const int lane = threadIdx.x, warp = threadIdx.y;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        e_d += __shfl_xor_sync(0xffffffffu, e_d, off);
+        e_f += __shfl_xor_sync(0xffffffffu, e_f, off);
+    }
+    if (lane == 0) {
+        sm.wsum_d[warp] = e_d;
+        sm.wsum_f[warp] = e_f;
+    }
+    __syncthreads();
+    if (warp == 0 && lane == 0) {
+        if (a.flags & kEnergyF32) {
+            float s = 0.0f;
+            for (int i = 0; i < kWarps; ++i) s += sm.wsum_f[i];
+            *static_cast<float*>(eslot) = s;
+        } else {
+            double s = 0.0;
+            for (int i = 0; i < kWarps; ++i) s += sm.wsum_d[i];
+            *static_cast<double*>(eslot) = s;
+        }
+    }
+}
+
+// Row order within a warp. With an even number R of rows per warp (and tile origins at even rows)
+// row rr of a warp has o = (rr + colour) & 1, so visiting rr = i ^ colour makes o = i & 1 a
+// compile-time constant of the unrolled loop over i. Odd R keeps the natural order, o at run time.
+template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R % 2 == 0) ? (i ^ c) : i; }
+
+// update_row of the i-th row in the order row_of(), with o fixed at compile time for even R (the
+// branch on i & 1 disappears when the caller's loop over i is unrolled).
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED>
+__device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
+                                             int lj, Pack4<S>& pk, uint32_t bits,
+                                             const TileSmem<R>& sm, double& e_d, float& e_f)
+{
+    if constexpr (R % 2 == 0) {
+        if (i & 1) update_row<S, R, MEASURE, SAMPLE, SCHED, 1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
+        else update_row<S, R, MEASURE, SAMPLE, SCHED, 0>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
+    } else {
+        update_row<S, R, MEASURE, SAMPLE, SCHED, -1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
+    }
+}
+
+// One tile (tile column tx, tile row ty) of colour a.colour, staged from global memory. With
+// MEASURE (black pass) the tile's sum of u_b . h_b over its existing black sites is written to
+// *eslot. Begins with a block barrier, so a block may call it for several tiles in a row.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R>& sm,
+                                           void* eslot)
+{
+    constexpr int TY = kWarps * R;
+    const int c = a.colour, cb = c ^ 1;
+    const int j0 = tx * kTJ;
+    const int y0 = ty * TY;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const S* __restrict__ other = static_cast<const S*>(a.other);
+    const S* __restrict__ own = static_cast<const S*>(a.own);
+    const int jb = j0 + 4 * lane;             // first of this thread's 4 columns
+    const int lj = 4 * lane;
+
+    // ---- own rows: values and frozen bits, loaded before the staging so their latency overlaps
+    Pack4<S> mine[R];   // in the order row_of()
+    uint32_t bits[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int y = y0 + warp * R + row_of<R>(i, c);
+        bits[i] = 0xFu;
+        if (y < a.Ly) {
+            load4(own + (size_t)y * a.pitch + jb, mine[i]);
+            bits[i] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
+        }
     }
 
-    if (MEASURE) {
+    __syncthreads();   // the previous tile's readers are done with sm
+    // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
+    // lies inside the lattice (nearly all) skip the per-entry bounds checks.
+    const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
+    if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
+    else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
+    __syncthreads();
+
+    double e_d = 0.0;
+    float e_f = 0.0f;
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            e_d += __shfl_xor_sync(0xffffffffu, e_d, off);
-            e_f += __shfl_xor_sync(0xffffffffu, e_f, off);
-        }
-        if (lane == 0) {
-            sm.wsum_d[warp] = e_d;
-            sm.wsum_f[warp] = e_f;
-        }
-        __syncthreads();
-        if (warp == 0 && lane == 0) {
-            if (a.flags & kEnergyF32) {
-                float s = 0.0f;
-                for (int i = 0; i < kWarps; ++i) s += sm.wsum_f[i];
-                *static_cast<float*>(eslot) = s;
-            } else {
-                double s = 0.0;
-                for (int i = 0; i < kWarps; ++i) s += sm.wsum_d[i];
-                *static_cast<double*>(eslot) = s;
-            }
-        }
+    for (int i = 0; i < R; ++i) {
+        const int ly = warp * R + row_of<R>(i, c);
+        const int y = y0 + ly;
+        if (y < a.Ly)
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED>(i, a, y, ly, jb, lj, mine[i], bits[i], sm, e_d, e_f);
     }
+    if (MEASURE) tile_energy<R>(a, e_d, e_f, sm, eslot);
 }
 
 }  // namespace f32

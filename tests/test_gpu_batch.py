@@ -108,6 +108,31 @@ def test_batch_problem0_equals_single_handle(mpr):
         mpr.mpr_destroy(h)
 
 
+@pytest.mark.parametrize("setup", ["SDS", "HDS"])
+def test_batch_equals_tma_single_handle(mpr, setup):
+    # Lattices wider than one tile run the single-handle sweeps through the TMA-fed persistent
+    # kernel (2100 x 1300: 738 tiles, more than one tile per block on 152 SMs); the batch stages
+    # with plain loads. Both apply the same per-site arithmetic, so problem 0's state, prediction
+    # and mean energy agree bit for bit.
+    probs = _problems([(2100, 1300, 0.9), (700, 45, 0.66), (64, 64, 0.33)], base=300)
+    b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], setup, seed=21)
+    h = mpr.mpr_create(probs[0].z, probs[0].mask)
+    try:
+        mpr.mpr_batch_fill(b, 12, 4, T=np.full(len(probs), 0.2))
+        mpr.mpr_set_options(h, setup, seed=21)
+        mpr.mpr_set_temperature(h, 0.2)
+        mpr.mpr_run(h, 12, 4)
+        single, _ = mpr.mpr_get_state(h)
+        got, sw = mpr.mpr_batch_get_state(b, 0)
+        assert sw == 16
+        assert np.array_equal(got, single)
+        assert np.array_equal(mpr.mpr_batch_predict(b, 0), mpr.mpr_predict(h))
+        assert mpr.mpr_batch_get_info(b, 0)["e_bond_mean"] == mpr.mpr_get_info(h)["e_bond_mean"]
+    finally:
+        mpr.mpr_batch_destroy(b)
+        mpr.mpr_destroy(h)
+
+
 def test_batch_tuning_matches_single_handle(mpr):
     probs = _problems()
     b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "SDS", seed=9)

@@ -179,7 +179,10 @@ def test_single_sweep_ddd(mpr, orc, Lx, Ly, p, T):
     assert np.array_equal(got[m].view(np.uint64), state[m].view(np.uint64))
 
 
-@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (257, 129, 0.66)])
+# Lattices with Lx > 256 run the TMA-fed kernel (300 x 45: ragged tile column and row; 2100 x 1300:
+# several tiles per block); the others the one-tile-per-block kernel.
+@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (257, 129, 0.66),
+                                     (300, 45, 0.66), (2100, 1300, 0.9)])
 @pytest.mark.parametrize("setup", ["SDS", "SSS", "SDD", "DDS"])
 def test_single_sweep_fp32_functions(mpr, orc, Lx, Ly, p, setup):
     T = 0.3
@@ -196,7 +199,8 @@ def test_single_sweep_fp32_functions(mpr, orc, Lx, Ly, p, setup):
     assert excused.sum() <= max(3, 2e-3 * Lx * Ly)
 
 
-@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9)])
+@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (300, 45, 0.66),
+                                     (2100, 1300, 0.9)])
 @pytest.mark.parametrize("setup", ["HDS", "BDS", "HSS"])
 def test_single_sweep_16bit_storage(mpr, orc, Lx, Ly, p, setup):
     # Red phase: identical inputs; the GPU result is its FP32 update rounded to the storage type.
@@ -464,3 +468,72 @@ def test_tall_thin_grid_beyond_grid_limits(mpr, orc):
         excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
         assert np.all(np.abs(got - exp)[~excused] <= (1e-9 if setup == "DDD" else 1e-4))
         assert np.array_equal(zhat[pr.mask == 1], pr.z[pr.mask == 1])
+
+
+# --- the two FP32 sweep kernels ------------------------------------------------------------
+
+def _kernel_run(mpr, pr, setup, state, kind, equil, samples, T=0.3):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=31)
+        mpr.mpr_set_sweep_kernel(h, kind)
+        mpr.mpr_set_state(h, state, 5)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, equil, samples)
+        got, sw = mpr.mpr_get_state(h)
+        info = mpr.mpr_get_info(h)
+        zhat = mpr.mpr_predict(h) if samples else None
+    finally:
+        mpr.mpr_destroy(h)
+    return got, sw, info, zhat
+
+
+@pytest.mark.parametrize("Lx,Ly,p", [(300, 45, 0.66), (2100, 1300, 0.9), (517, 34, 0.33)])
+@pytest.mark.parametrize("setup", ["HDS", "SDS", "DDS", "BDS"])
+def test_tma_kernel_equals_tile_kernel(mpr, orc, Lx, Ly, p, setup):
+    # The TMA-fed persistent kernel (kind 1: 128 x 32 tiles, several per block at 2100 x 1300,
+    # ragged last tile column and row) and the one-tile-per-block kernel (kind 0) apply the same
+    # per-site arithmetic: states after plain sweeps, and predictions and energies after sampling
+    # sweeps (whose energy passes always run kind 0), agree bit for bit.
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=41, mask_seed=42)
+    _, state = _start_state(orc, pr, setup, 31)
+    g0, s0, i0, z0 = _kernel_run(mpr, pr, setup, state, 0, 6, 3)
+    g1, s1, i1, z1 = _kernel_run(mpr, pr, setup, state, 1, 6, 3)
+    assert i0["sweep_kernel"] == 0 and i1["sweep_kernel"] == 1
+    assert s0 == s1 == 14
+    assert np.array_equal(g0, g1)
+    assert np.array_equal(z0, z1)
+    assert i0["e_bond_mean"] == i1["e_bond_mean"]
+
+
+def test_sweep_kernel_choice(mpr, orc):
+    pr = mpr_inputs.make_problem(700, 300, 0.9, field_seed=43, mask_seed=44)
+    _, state = _start_state(orc, pr, "HDS", 31)
+    # automatic: the first run of >= 12 plain sweeps times both kernels inside the chain
+    ga, _, ia, _ = _kernel_run(mpr, pr, "HDS", state, -1, 20, 0)
+    g0, _, _, _ = _kernel_run(mpr, pr, "HDS", state, 0, 20, 0)
+    assert ia["sweep_kernel"] in (0, 1)
+    assert np.array_equal(ga, g0)
+    # not chosen yet after a short run
+    _, _, ib, _ = _kernel_run(mpr, pr, "HDS", state, -1, 3, 0)
+    assert ib["sweep_kernel"] == -1
+    # kind 1 needs FP32 functions and a lattice wider than one tile with >= 34 rows
+    for shape, setup in [((256, 300), "HDS"), ((700, 33), "SDS"), ((700, 300), "DDD")]:
+        q = mpr_inputs.make_problem(*shape, 0.5, field_seed=45, mask_seed=46)
+        h = mpr.mpr_create(q.z, q.mask)
+        try:
+            mpr.mpr_set_options(h, setup, seed=1)
+            with pytest.raises(mpr.MPRError) as e:
+                mpr.mpr_set_sweep_kernel(h, 1)
+            assert e.value.status == mpr.MPR_ERR_INVALID_ARG
+            mpr.mpr_set_sweep_kernel(h, 0)
+            assert mpr.mpr_get_info(h)["sweep_kernel"] == (-1 if setup == "DDD" else 0)
+        finally:
+            mpr.mpr_destroy(h)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        for bad in (-2, 2):
+            with pytest.raises(mpr.MPRError):
+                mpr.mpr_set_sweep_kernel(h, bad)
+    finally:
+        mpr.mpr_destroy(h)
