@@ -30,7 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SM_COUNT = 152
-MUFU_PER_CLK_PER_SM = 16          # sin/cos/ex2/rcp/rsqrt lanes per SM per clock
+# MUFU lanes per SM per clock when the probe cannot run: sin/cos/rcp 16; ex2 32 on this part
+# (the probe measured 15.9 and 31.7 on GB300)
+MUFU_FALLBACK_PER_CLK = {"sin": 16, "cos": 16, "ex2": 32, "rcp": 16}
 STORE_BYTES = {"D": 8, "S": 4, "H": 2, "B": 2}
 
 
@@ -54,6 +56,8 @@ def parse():
                     help="single: one L x L field; batch: many uneven problems in one launch")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true", help="batch: default launch shape")
+    ap.add_argument("--sweep-kernel", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP32 sweep kernel: -1 automatic (timed per job), 0 tile per block, 1 TMA-fed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -191,6 +195,26 @@ def stored_traffic(kernel_id: str, kernel: str, workload: str):
 SWEEP_KERNELS = {-1: "mpr::sweep_kernel", 0: "mpr::sweep_f32_kernel", 1: "mpr::sweep_f32_tma_kernel"}
 
 
+def mufu_rates(local_rank: int, sm_mhz_max: float):
+    """Special-function throughput (ops/s) measured by the probe that build() compiles
+    (paper_1910_08448_gb300/probe/mufu_rate.cu), on this rank's GPU; nominal lanes x clock if it
+    cannot run."""
+    exe = os.path.join(ROOT, "paper_1910_08448_gb300", "_build", "mufu_rate")
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES=str(local_rank))
+    if "CUDA_VISIBLE_DEVICES" in os.environ:
+        vis = os.environ["CUDA_VISIBLE_DEVICES"].split(",")
+        env["CUDA_VISIBLE_DEVICES"] = vis[local_rank] if local_rank < len(vis) else vis[0]
+    try:
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=60, env=env)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        rates = {k: d[f"{k}_per_s"] for k in ("sin", "cos", "ex2", "rcp")}
+        if all(v > 0 for v in rates.values()):
+            return rates, "probe"
+    except (OSError, ValueError, KeyError, IndexError, subprocess.SubprocessError):
+        pass
+    return {k: SM_COUNT * v * sm_mhz_max * 1e6 for k, v in MUFU_FALLBACK_PER_CLK.items()}, "nominal"
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -223,6 +247,8 @@ def run_mine(args, dist: Dist):
         h = mpr.mpr_create_dev(zt, mt)
         try:
             mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+            if args.sweep_kernel >= 0:
+                mpr.mpr_set_sweep_kernel(h, args.sweep_kernel)
             mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
             if profile:
                 mpr.mpr_set_profiling(h, True)
@@ -269,11 +295,16 @@ def run_mine(args, dist: Dist):
     N = L * L
     b = STORE_BYTES[args.setup[0]]
     bytes_launch = (N / 2) * (b * (2 + p) + 1 / 8)
-    mufu_launch = (N / 2) * (2 + 6 * p)
     hbm_gbs, sm_mhz_max, src = peaks()
-    mufu_peak = SM_COUNT * MUFU_PER_CLK_PER_SM * sm_mhz_max * 1e6          # ops/s
+    # MUFU work of one pass: every site's sin/cos once (staged as a neighbour); per prediction
+    # site its own sin/cos, the proposal's sin/cos, one ex2 and one rcp. Each at its own measured
+    # rate; expressed in sin-equivalent operations at the sin rate.
+    rates, mufu_src = mufu_rates(dist.local, sm_mhz_max)
+    r_sc = min(rates["sin"], rates["cos"])
+    t_mufu = (N / 2) * (2 / r_sc + p * (4 / r_sc + 1 / rates["ex2"] + 1 / rates["rcp"]))
+    mufu_launch = t_mufu * r_sc
+    mufu_peak = r_sc
     t_hbm = bytes_launch / (hbm_gbs * 1e9)
-    t_mufu = mufu_launch / mufu_peak
     kid = sweep_kernel_id()
     kname = SWEEP_KERNELS[infos[-1]["sweep_kernel"]]
     workload = f"L{L}_p{p}_{args.setup}"
@@ -283,13 +314,15 @@ def run_mine(args, dist: Dist):
                 "unit": "GB/s"}
     else:
         roof = {"bound": "alu", "achieved": mufu_launch / t_launch / 1e9,
-                "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)"}
+                "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU, sin-equivalent)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof.update({"traffic": traffic, "peak_source": src, "kernel": kname,
+    roof.update({"traffic": traffic, "peak_source": src if roof["bound"] == "hbm" else mufu_src,
+                 "kernel": kname,
                  "launch_us": t_launch * 1e6, "algorithmic_bytes_per_launch": bytes_launch,
                  "algorithmic_mufu_per_launch": mufu_launch, "kernel_id": kid,
                  "hbm_frac": bytes_launch / t_launch / 1e9 / hbm_gbs,
-                 "mufu_frac": mufu_launch / t_launch / mufu_peak})
+                 "mufu_frac": mufu_launch / t_launch / mufu_peak,
+                 "mufu_rates_per_s": rates, "mufu_rates_source": mufu_src})
 
     # ---- FP64 (DDD) GPU path on the same lattice: speedup of the sweep kernel ----
     T_last = infos[-1]["T"]
@@ -331,6 +364,8 @@ def run_mine(args, dist: Dist):
             h = mpr.mpr_create(zn, mn)
             try:
                 mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
+                if args.sweep_kernel >= 0:
+                    mpr.mpr_set_sweep_kernel(h, args.sweep_kernel)
                 mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
                 mpr.mpr_tune_temperature(h)
                 mpr.mpr_run(h, args.equil, args.samples)
@@ -385,10 +420,10 @@ def run_batch(args, dist):
     try:
         mpr.mpr_batch_set_tuning(b, n_eq=args.tune_eq, n_meas=args.tune_meas)
         if args.no_autotune:
-            rows, bps, mode = 2, 0, 2
-            mpr.mpr_batch_set_launch(b, rows, bps, mode)
+            rows, cols, bps, mode = 32, 128, 0, 2
+            mpr.mpr_batch_set_launch(b, rows, cols, bps, mode)
         else:
-            rows, bps, mode = mpr.mpr_batch_autotune(b, 10)
+            rows, cols, bps, mode = mpr.mpr_batch_autotune(b, 10)
 
         fills = []
 
@@ -430,7 +465,7 @@ def run_batch(args, dist):
     for p, o in zip(probs, outs):
         pred = p.mask == 0
         maes.append(float(np.mean(np.abs(o - p.z)[pred])))
-    return {"value": upd / (ms / 1e3), "ms": ms, "rows": rows, "blocks_per_sm": bps, "mode": mode,
+    return {"value": upd / (ms / 1e3), "ms": ms, "tile": [rows, cols], "blocks_per_sm": bps, "mode": mode,
             "clocks": clk.summary(), "n_problems": len(probs),
             "sites": int(sum(p.z.size for p in probs)),
             "pred_sites": int(sum(int((p.mask == 0).sum()) for p in probs)),
@@ -511,10 +546,11 @@ def main():
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"{res['n_problems']} independent problems, side "
                                        "log-uniform 64..1024, aspect <= 4:1, p in {0.33,0.66,0.9}, "
-                                       "kappa in [0.05,0.5]; one persistent launch per step (tune + "
+                                       "kappa in [0.05,0.5]; one launch per step (tune + "
                                        f"{args.equil} equil + {args.samples} samples) + predictions",
                            "setup": args.setup, "acc": args.acc, "sites": res["sites"],
-                           "pred_sites": res["pred_sites"], "autotuned_rows": res["rows"],
+                           "pred_sites": res["pred_sites"],
+                           "autotuned_tile_rows_x_cols": res["tile"],
                            "autotuned_blocks_per_sm": res["blocks_per_sm"],
                            "autotuned_mode": ["persistent cooperative kernel",
                                               "persistent kernel in a one-node graph",

@@ -152,7 +152,8 @@ mpr_status mpr_set_profiling(mpr_handle h, int on);
  *         updates the current one. Needs a lattice at least two tiles wide (Lx > 256) and 34 rows.
  * kind -1 (default): automatic. The first run of at least 12 sweeps without energy or sample
  *         work (an equilibration, or a tuning probe's) times 5 sweeps of each kernel after one
- *         warm-up sweep each, as ordinary sweeps of the chain, and keeps the faster.
+ *         warm-up sweep each, as ordinary sweeps of the chain, and keeps kind 1 only if it is
+ *         more than 2 % faster.
  * INVALID_ARG if kind is not -1, 0 or 1, or kind 1 is unavailable for the handle. A forced kind
  * stays across mpr_set_options while it remains available; an automatic choice is redone. */
 mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind);
@@ -174,9 +175,12 @@ mpr_status mpr_philox4x32_10_dev(const uint32_t* ctr_dev, uint32_t* out_dev, int
  * mask and temperature; problem i draws its random numbers from the Philox stream with problem id
  * i (so problem 0 of a batch follows the same chain as a single handle with the same options).
  * The batch computes with FP32 functions (opt->func must be MPR_PREC_S); storage, energy and
- * accumulator precision are free. The whole fill is ONE cooperative kernel launch whose blocks
- * meet at grid barriers between colour passes; a barrier wait is bounded (2 s by default) and a
- * wait that runs out ends the launch with MPR_ERR_DEVICE_TIMEOUT (the batch is then unusable).
+ * accumulator precision are free. The whole fill is ONE launch: by default a CUDA graph whose
+ * device-side while loop repeats a red pass, a black pass (one block per tile of every unfinished
+ * problem) and a finish kernel until every problem is done; or one persistent cooperative kernel
+ * whose blocks meet at grid barriers between colour passes. A barrier wait is bounded (2 s by
+ * default) and a wait that runs out ends the launch with MPR_ERR_DEVICE_TIMEOUT (the batch is then
+ * unusable).
  * --------------------------------------------------------------------------------------------- */
 typedef struct mpr_batch_ctx* mpr_batch;
 
@@ -188,16 +192,19 @@ mpr_status mpr_batch_create(int n, const int* Lx, const int* Ly, const double* c
 void mpr_batch_destroy(mpr_batch b);
 mpr_status mpr_batch_set_stream(mpr_batch b, void* stream);
 mpr_status mpr_batch_set_tuning(mpr_batch b, const mpr_tuning* t);
-/* Launch shape: tile rows per warp (1, 2 or 4: tiles of 128 x 8*rows half-lattice entries),
- * blocks per SM (persistent modes; 0 = occupancy limit) and mode: 0 = one persistent cooperative
- * kernel (blocks walk the tiles, grid barriers between colour passes), 1 = the same kernel as a
- * one-node CUDA graph, 2 (default) = one CUDA graph whose device-side while loop repeats a red
- * pass, a black pass (one block per tile) and a finish kernel until every problem is done. */
-mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int use_graph);
-/* Autotuner: times `sweeps` sweeps of every launch shape and mode on a copy of the batch state
- * (the chains are left as they were), keeps the fastest, and caches it for batches of the same
- * signature. */
-mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* blocks_per_sm_out);
+/* Launch shape: the tile in half-lattice entries, tile_rows x tile_cols = 8, 16 or 32 x 128, or
+ * 16 or 32 x 64 (64-column tiles waste less of narrow problems; default 32 x 128), blocks per SM
+ * (persistent modes; 0 = occupancy limit) and mode: 0 = one persistent cooperative kernel (blocks
+ * walk the tiles, grid barriers between colour passes), 1 = the same kernel as a one-node CUDA
+ * graph, 2 (default) = one CUDA graph whose device-side while loop repeats a red pass, a black
+ * pass (one block per tile) and a finish kernel until every problem is done. */
+mpr_status mpr_batch_set_launch(mpr_batch b, int tile_rows, int tile_cols, int blocks_per_sm,
+                                int use_graph);
+/* Autotuner: times `sweeps` sweeps of every tile shape and mode (persistent modes at every
+ * residency) on a copy of the batch state (the chains are left as they were), keeps the fastest,
+ * and caches it for batches of the same signature. Any output pointer may be NULL. */
+mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* tile_rows_out, int* tile_cols_out,
+                              int* blocks_per_sm_out);
 /* One launch: with T == NULL every problem is tuned first (as mpr_tune_temperature), else T[i]
  * is used; then equil sweeps and samples accumulated sweeps (as mpr_run). T_out[i] and
  * status_out[i] (either may be NULL) receive each problem's temperature and tuning status.
@@ -211,8 +218,8 @@ mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info);
 /* The last fill's launch: iterations (sweeps of the longest-running problem), device time in ms
  * (CUDA events on the batch's stream), and the launch shape and mode it used. Any pointer may be
  * NULL. */
-mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* rows,
-                               int* blocks_per_sm, int* mode);
+mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* tile_rows,
+                               int* tile_cols, int* blocks_per_sm, int* mode);
 /* Fault injection for tests of the timeout path: the next fill expects `extra_arrivals` more
  * blocks at every grid barrier than exist (so the first barrier cannot complete) and waits at most
  * timeout_s seconds. Nothing faults or hangs: the launch ends and reports MPR_ERR_DEVICE_TIMEOUT. */

@@ -104,13 +104,13 @@ def load():
             "mpr_batch_destroy": ([H], None),
             "mpr_batch_set_stream": ([H, vp], i),
             "mpr_batch_set_tuning": ([H, P(mpr_tuning)], i),
-            "mpr_batch_set_launch": ([H, i, i, i], i),
-            "mpr_batch_autotune": ([H, i, P(i), P(i)], i),
+            "mpr_batch_set_launch": ([H, i, i, i, i], i),
+            "mpr_batch_autotune": ([H, i, P(i), P(i), P(i)], i),
             "mpr_batch_fill": ([H, vp, i, i, vp, vp], i),
             "mpr_batch_predict": ([H, i, vp], i),
             "mpr_batch_get_state": ([H, i, vp, P(u32)], i),
             "mpr_batch_get_info": ([H, i, P(mpr_info)], i),
-            "mpr_batch_get_stats": ([H, P(i), P(d), P(i), P(i), P(i)], i),
+            "mpr_batch_get_stats": ([H, P(i), P(d), P(i), P(i), P(i), P(i)], i),
             "mpr_batch_inject_barrier_fault": ([H, i, d], i),
             "mpr_status_string": ([i], ctypes.c_char_p),
             "mpr_last_error": ([], ctypes.c_char_p),
@@ -350,17 +350,19 @@ def mpr_batch_set_tuning(b, n_eq=200, n_meas=50, T_lo=1e-3, T_hi=10.0, rel_tol=1
     _check(load().mpr_batch_set_tuning(b, ctypes.byref(t)))
 
 
-def mpr_batch_set_launch(b, rows: int = 2, blocks_per_sm: int = 0, mode: int = 2):
-    """mode 0: persistent cooperative kernel, 1: the same as a one-node graph, 2: graph with a
-    device-side while loop over per-pass kernels."""
-    _check(load().mpr_batch_set_launch(b, rows, blocks_per_sm, int(mode)))
+def mpr_batch_set_launch(b, tile_rows: int = 32, tile_cols: int = 128, blocks_per_sm: int = 0,
+                         mode: int = 2):
+    """Tile of tile_rows x tile_cols half-lattice entries (8/16/32 x 128 or 16/32 x 64); mode 0:
+    persistent cooperative kernel, 1: the same as a one-node graph, 2: graph with a device-side
+    while loop over per-pass kernels."""
+    _check(load().mpr_batch_set_launch(b, tile_rows, tile_cols, blocks_per_sm, int(mode)))
 
 
 def mpr_batch_autotune(b, sweeps: int = 10):
-    """Returns (rows, blocks_per_sm, mode) of the fastest launch shape."""
-    r, k = ctypes.c_int(), ctypes.c_int()
-    _check(load().mpr_batch_autotune(b, sweeps, ctypes.byref(r), ctypes.byref(k)))
-    return r.value, k.value, mpr_batch_get_stats(b)["mode"]
+    """Returns (tile_rows, tile_cols, blocks_per_sm, mode) of the fastest launch shape."""
+    r, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().mpr_batch_autotune(b, sweeps, ctypes.byref(r), ctypes.byref(c), ctypes.byref(k)))
+    return r.value, c.value, k.value, mpr_batch_get_stats(b)["mode"]
 
 
 def mpr_batch_fill(b, equil: int, samples: int, T=None):
@@ -396,11 +398,12 @@ def mpr_batch_get_info(b, i: int) -> dict:
 
 
 def mpr_batch_get_stats(b) -> dict:
-    it, ms, r, k, m = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    it, ms = ctypes.c_int(), ctypes.c_double()
+    r, c, k, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().mpr_batch_get_stats(b, ctypes.byref(it), ctypes.byref(ms), ctypes.byref(r),
-                                      ctypes.byref(k), ctypes.byref(m)))
-    return {"iterations": it.value, "fill_ms": ms.value, "rows": r.value, "blocks_per_sm": k.value,
-            "mode": m.value}
+                                      ctypes.byref(c), ctypes.byref(k), ctypes.byref(m)))
+    return {"iterations": it.value, "fill_ms": ms.value, "tile_rows": r.value, "tile_cols": c.value,
+            "blocks_per_sm": k.value, "mode": m.value}
 
 
 def mpr_batch_inject_barrier_fault(b, extra_arrivals: int = 1, timeout_s: float = 0.05):

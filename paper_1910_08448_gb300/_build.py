@@ -1,4 +1,5 @@
-"""Builds libmpr.so in-tree for sm_103a: one nvcc process per translation unit, then a link."""
+"""Builds libmpr.so in-tree for sm_103a (one nvcc process per translation unit, then a link) and
+the MUFU throughput probe that bench.py runs for its roofline (_build/mufu_rate)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -11,6 +12,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmpr.so")
+PROBE_SRC = os.path.join(PKG, "probe", "mufu_rate.cu")
+PROBE = os.path.join(BUILD, "mufu_rate")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,10 +40,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE))
+    return all(os.path.getmtime(f) <= t for f in _deps() + [PROBE_SRC])
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
@@ -61,8 +64,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stderr)
         return obj
 
+    def compile_probe():
+        tmp = PROBE + f".tmp{os.getpid()}"
+        r = subprocess.run([cc, *ARCH, "-O3", "-std=c++17", PROBE_SRC, "-o", tmp],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stderr}")
+        os.replace(tmp, PROBE)
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        probe = ex.submit(compile_probe)
         objs = list(ex.map(compile_one, sources()))
+        probe.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]

@@ -442,7 +442,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
         CU(cudaEventSynchronize(h->cal[3]));
         for (int kind = 0; kind < 2; ++kind)
             CU(cudaEventElapsedTime(&ms[kind], h->cal[2 * kind], h->cal[2 * kind + 1]));
-        h->sweep_kind = ms[1] < ms[0] ? 1 : 0;
+        h->sweep_kind = ms[1] < 0.98f * ms[0] ? 1 : 0;   // the TMA kernel only when clearly faster
     }
     const int kind = !tma_ok ? 0 : h->sweep_force >= 0 ? h->sweep_force : (h->sweep_kind > 0 ? 1 : 0);
     for (; k < n; ++k) CHECK(one(k, kind));

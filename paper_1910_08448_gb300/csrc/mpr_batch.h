@@ -80,17 +80,37 @@ struct Args {
     float qf;
 };
 
+// Tile shapes of the batched kernels: half-lattice columns and rows per thread; the tile height
+// is 8 warps x (128 / cols) x rows per thread (a warp step covers one 128-column row or two
+// 64-column rows). Index = the shape id used by the launch functions below.
+struct Shape {
+    int cols, rpt;
+};
+constexpr int kShapes = 5;
+constexpr Shape kShape[kShapes] = {{128, 1}, {128, 2}, {128, 4}, {64, 1}, {64, 2}};
+constexpr int shape_rows(int s) { return 8 * (128 / kShape[s].cols) * kShape[s].rpt; }
+constexpr int shape_cols(int s) { return kShape[s].cols; }
+
+// The kernels of one storage type and tile shape: graph-mode pass kernel, persistent kernel, and
+// their dynamic shared memory. One function per storage type (mpr_batch_<type>.cu).
+struct Kernels {
+    const void* pass;
+    const void* persistent;
+    size_t smem;
+};
+Kernels kernels_f16(int shape);
+Kernels kernels_bf16(int shape);
+Kernels kernels_f32(int shape);
+Kernels kernels_f64(int shape);
+
 }  // namespace batch
 
-int batch_tile_rows(int rows);
-int batch_tile_cols();
-size_t batch_smem_bytes(int rows);
-cudaError_t batch_occupancy(int store, int rows, int* blocks_per_sm);
-cudaError_t batch_launch(int store, int rows, int grid, const batch::Args* args_dev, cudaStream_t st,
+cudaError_t batch_occupancy(int store, int shape, int* blocks_per_sm);
+cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args_dev, cudaStream_t st,
                          bool use_graph);
 // Graph mode: an executable graph whose device-side while loop runs red pass, black pass and the
 // finish kernel until no problem is active (or max_iters). max_tiles = blocks of a pass kernel.
-cudaError_t batch_graph_build(int store, int rows, int max_tiles, const batch::Args* args_dev,
+cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::Args* args_dev,
                               cudaGraphExec_t* out);
 
 }  // namespace mpr

@@ -65,12 +65,13 @@ struct mpr_batch_ctx {
     mpr_tuning tune{};
     cudaStream_t stream = nullptr;
     bool broken = false;
-    int rows = 2, bps = 0, use_graph = 2;    // launch shape (rows per warp, blocks per SM) and
-                                             // mode: 0/1 persistent kernel (direct / one-node
-                                             // graph), 2 graph with a device-side while loop
-    cudaGraphExec_t gexec[5] = {};           // graph-mode executables per rows (1, 2, 4)
-    int gexec_tiles[5] = {};
-    int tiled_rows = 0;                      // rows of the current tile list
+    int shape = 2, bps = 0, use_graph = 2;   // launch shape (tile shape id of batch::kShape,
+                                             // blocks per SM) and mode: 0/1 persistent kernel
+                                             // (direct / one-node graph), 2 graph with a
+                                             // device-side while loop
+    cudaGraphExec_t gexec[batch::kShapes] = {};   // graph-mode executables per tile shape
+    int gexec_tiles[batch::kShapes] = {};
+    int tiled_shape = -1;                    // tile shape of the current tile list
     int bar_extra = 0;
     double timeout_s = 2.0;
     int last_iters = 0;                      // iterations of the last fill's launch
@@ -149,12 +150,12 @@ Layout layout_of(const Prob& p)
     return L;
 }
 
-// Tile list for `rows` rows per warp: problem by problem, row-major tiles; then the order in
-// which the blocks take them: by the number of lattice entries they cover, largest first.
-mpr_status build_tiles(mpr_batch_ctx* b, int rows)
+// Tile list for a tile shape: problem by problem, row-major tiles; then the order in which the
+// blocks take them: by the number of lattice entries they cover, largest first.
+mpr_status build_tiles(mpr_batch_ctx* b, int shape)
 {
-    if (b->tiled_rows == rows) return MPR_OK;
-    const int TY = batch_tile_rows(rows), TJ = batch_tile_cols();
+    if (b->tiled_shape == shape) return MPR_OK;
+    const int TY = batch::shape_rows(shape), TJ = batch::shape_cols(shape);
     b->tile_prob.clear();
     std::vector<long long> cost;
     for (int i = 0; i < b->n; ++i) {
@@ -190,7 +191,7 @@ mpr_status build_tiles(mpr_batch_ctx* b, int rows)
     }
     BCU(cudaMemcpyAsync(b->d_tile_prob, b->tile_prob.data(), (size_t)b->ntiles * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream));
-    b->tiled_rows = rows;
+    b->tiled_shape = shape;
     return MPR_OK;
 }
 
@@ -198,7 +199,7 @@ mpr_status default_shape(mpr_batch_ctx* b)
 {
     if (b->bps > 0) return MPR_OK;
     int occ = 0;
-    BCU(batch_occupancy(b->prec.store, b->rows, &occ));
+    BCU(batch_occupancy(b->prec.store, b->shape, &occ));
     if (occ < 1) return bfail(MPR_ERR_CUDA, "batched kernel cannot be resident on an SM");
     b->bps = occ;
     return MPR_OK;
@@ -208,9 +209,9 @@ mpr_status default_shape(mpr_batch_ctx* b)
 mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, float* ms_out)
 {
     BCHECK(default_shape(b));
-    BCHECK(build_tiles(b, b->rows));
+    BCHECK(build_tiles(b, b->shape));
     int occ = 0;
-    BCU(batch_occupancy(b->prec.store, b->rows, &occ));
+    BCU(batch_occupancy(b->prec.store, b->shape, &occ));
     const int bps = b->bps < occ ? b->bps : occ;
     const int grid = b->sms * bps;
     int active = 0;
@@ -269,18 +270,18 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
         if (!b->dArgs) BCHECK(balloc(b, &b->dArgs, sizeof(batch::Args)));
         BCU(cudaMemcpyAsync(b->dArgs, &A, sizeof A, cudaMemcpyHostToDevice, b->stream));
         if (b->use_graph == 2) {
-            cudaGraphExec_t& ge = b->gexec[b->rows];
-            if (ge && b->gexec_tiles[b->rows] != b->ntiles) {
+            cudaGraphExec_t& ge = b->gexec[b->shape];
+            if (ge && b->gexec_tiles[b->shape] != b->ntiles) {
                 cudaGraphExecDestroy(ge);
                 ge = nullptr;
             }
             if (!ge) {
-                BCU(batch_graph_build(b->prec.store, b->rows, b->ntiles, b->dArgs, &ge));
-                b->gexec_tiles[b->rows] = b->ntiles;
+                BCU(batch_graph_build(b->prec.store, b->shape, b->ntiles, b->dArgs, &ge));
+                b->gexec_tiles[b->shape] = b->ntiles;
             }
             BCU(cudaGraphLaunch(ge, b->stream));
         } else {
-            BCU(batch_launch(b->prec.store, b->rows, grid, b->dArgs, b->stream, b->use_graph != 0));
+            BCU(batch_launch(b->prec.store, b->shape, grid, b->dArgs, b->stream, b->use_graph != 0));
         }
         b->launches += 1;
     }
@@ -511,7 +512,7 @@ mpr_status mpr_batch_set_stream(mpr_batch b, void* stream)
     if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
     BCU(cudaStreamSynchronize(b->stream));
     b->stream = static_cast<cudaStream_t>(stream);
-    b->tiled_rows = 0;   // re-upload the tile list on the new stream
+    b->tiled_shape = -1;   // re-upload the tile list on the new stream
     return MPR_OK;
 }
 
@@ -525,16 +526,23 @@ mpr_status mpr_batch_set_tuning(mpr_batch b, const mpr_tuning* t)
     return MPR_OK;
 }
 
-mpr_status mpr_batch_set_launch(mpr_batch b, int rows, int blocks_per_sm, int use_graph)
+mpr_status mpr_batch_set_launch(mpr_batch b, int tile_rows, int tile_cols, int blocks_per_sm,
+                                int use_graph)
 {
     if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
-    if (rows != 1 && rows != 2 && rows != 4) return bfail(MPR_ERR_INVALID_ARG, "rows must be 1, 2 or 4");
+    int shape = -1;
+    for (int s = 0; s < batch::kShapes; ++s)
+        if (batch::shape_rows(s) == tile_rows && batch::shape_cols(s) == tile_cols) shape = s;
+    if (shape < 0)
+        return bfail(MPR_ERR_INVALID_ARG,
+                     "tile %d x %d: use 8, 16 or 32 rows x 128 columns, or 16 or 32 rows x 64 columns",
+                     tile_rows, tile_cols);
     int occ = 0;
-    BCU(batch_occupancy(b->prec.store, rows, &occ));
+    BCU(batch_occupancy(b->prec.store, shape, &occ));
     if (blocks_per_sm < 0 || blocks_per_sm > occ)
         return bfail(MPR_ERR_INVALID_ARG, "blocks per SM must be in [0, %d] (0 = occupancy limit)", occ);
     if (use_graph < 0 || use_graph > 2) return bfail(MPR_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
-    b->rows = rows;
+    b->shape = shape;
     b->bps = blocks_per_sm;
     b->use_graph = use_graph;
     return MPR_OK;
@@ -570,7 +578,8 @@ mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, 
     return MPR_OK;
 }
 
-mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* blocks_per_sm_out)
+mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* tile_rows_out, int* tile_cols_out,
+                              int* blocks_per_sm_out)
 {
     if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
     if (b->broken) return bfail(MPR_ERR_STATE, "the batch was left undefined by a device timeout");
@@ -582,10 +591,11 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            b->rows = std::get<0>(it->second);
+            b->shape = std::get<0>(it->second);
             b->bps = std::get<1>(it->second);
             b->use_graph = std::get<2>(it->second);
-            if (rows_out) *rows_out = b->rows;
+            if (tile_rows_out) *tile_rows_out = batch::shape_rows(b->shape);
+            if (tile_cols_out) *tile_cols_out = batch::shape_cols(b->shape);
             if (blocks_per_sm_out) *blocks_per_sm_out = b->bps;
             return MPR_OK;
         }
@@ -599,12 +609,11 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
     std::vector<double> T((size_t)b->n);
     for (int i = 0; i < b->n; ++i) T[(size_t)i] = keep[(size_t)i].d.T > 0 ? keep[(size_t)i].d.T : 0.5;
     float best = 1e30f;
-    int best_rows = b->rows, best_bps = b->bps, best_mode = b->use_graph;
-    const int rows_c[3] = {1, 2, 4};
+    int best_shape = b->shape, best_bps = b->bps, best_mode = b->use_graph;
     mpr_status st = MPR_OK;
-    for (int r : rows_c) {
+    for (int r = 0; r < batch::kShapes; ++r) {
         // graph mode (one block per tile, device-side loop)
-        b->rows = r;
+        b->shape = r;
         b->bps = 0;
         b->use_graph = 2;
         prepare_fill(b, T.data());
@@ -613,7 +622,7 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
         if (st != MPR_OK) break;
         if (ms < best) {
             best = ms;
-            best_rows = r;
+            best_shape = r;
             best_bps = 0;
             best_mode = 2;
         }
@@ -621,7 +630,7 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
         int occ = 0;
         if (batch_occupancy(b->prec.store, r, &occ) != cudaSuccess) continue;
         for (int bps = 1; bps <= occ; ++bps) {
-            b->rows = r;
+            b->shape = r;
             b->bps = bps;
             b->use_graph = 0;
             prepare_fill(b, T.data());
@@ -629,7 +638,7 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
             if (st != MPR_OK) break;
             if (ms < best) {
                 best = ms;
-                best_rows = r;
+                best_shape = r;
                 best_bps = bps;
                 best_mode = 0;
             }
@@ -640,16 +649,17 @@ mpr_status mpr_batch_autotune(mpr_batch b, int sweeps, int* rows_out, int* block
     cudaStreamSynchronize(b->stream);
     cudaFree(saved);
     b->P = keep;
-    b->tiled_rows = 0;   // the restored table holds an older tile layout: rebuild on next fill
+    b->tiled_shape = -1;   // the restored table holds an older tile layout: rebuild on next fill
     if (st != MPR_OK) return st;
-    b->rows = best_rows;
+    b->shape = best_shape;
     b->bps = best_bps;
     b->use_graph = best_mode;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[key] = std::make_tuple(best_rows, best_bps, best_mode);
+        g_tune_cache[key] = std::make_tuple(best_shape, best_bps, best_mode);
     }
-    if (rows_out) *rows_out = best_rows;
+    if (tile_rows_out) *tile_rows_out = batch::shape_rows(best_shape);
+    if (tile_cols_out) *tile_cols_out = batch::shape_cols(best_shape);
     if (blocks_per_sm_out) *blocks_per_sm_out = best_bps;
     return MPR_OK;
 }
@@ -715,14 +725,15 @@ mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info)
     return MPR_OK;
 }
 
-mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* rows,
-                               int* blocks_per_sm, int* mode)
+mpr_status mpr_batch_get_stats(mpr_batch b, int* iterations, double* fill_ms, int* tile_rows,
+                               int* tile_cols, int* blocks_per_sm, int* mode)
 {
     if (!b) return bfail(MPR_ERR_INVALID_ARG, "batch is NULL");
     if (mode) *mode = b->use_graph;
     if (iterations) *iterations = b->last_iters;
     if (fill_ms) *fill_ms = (double)b->last_ms;
-    if (rows) *rows = b->rows;
+    if (tile_rows) *tile_rows = batch::shape_rows(b->shape);
+    if (tile_cols) *tile_cols = batch::shape_cols(b->shape);
     if (blocks_per_sm) *blocks_per_sm = b->bps;
     return MPR_OK;
 }

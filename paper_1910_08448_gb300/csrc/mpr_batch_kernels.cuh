@@ -1,0 +1,452 @@
+// mpr_batch_kernels.cuh -- device code of the batched launch: many independent gap-filling
+// problems in one launch (included by the per-storage translation units mpr_batch_<type>.cu, which
+// instantiate the kernels of one spin storage type each so the four compile in parallel, and by
+// mpr_batch.cu for the list compaction of its finish kernel).
+//
+// Every problem of a batch runs the whole method of Sec. 2 -- temperature tuning (bisection on
+// e_b(T) = e_s), equilibration, sampling -- inside one launch. Each iteration is one hybrid sweep
+// of every problem that is not finished: red tiles of all active problems, then black tiles. The
+// block that completes the last black tile of a problem (per-problem arrival counter) sums that
+// problem's tile energy partials in a fixed order and advances its state machine: probe
+// bookkeeping and the bisection step in FP64 (the same arithmetic as the single-problem host
+// loop), then equilibration, sampling, done. Problems of uneven size finish at different
+// iterations; their tiles leave the list.
+//
+// Persistent mode: one cooperative kernel whose blocks meet at a grid barrier between passes; the
+// barrier spins with a time limit, and a wait that runs out sets an error word, every block
+// leaves, the kernel ends normally and the host reports MPR_ERR_DEVICE_TIMEOUT.
+#pragma once
+
+#include "mpr.h"
+#include "mpr_batch.h"
+#include "mpr_tile_f32.cuh"
+
+namespace mpr {
+namespace batch {
+namespace {
+
+using namespace f32;
+
+__device__ __forceinline__ long long globaltimer_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded grid barrier (all blocks co-resident: cooperative launch). Thread 0 arrives, waits with
+// a time limit and publishes the error word to its block through shared memory, so every thread
+// of a block sees the same answer. The fences on both sides order this block's writes before the
+// arrival and the other blocks' writes before this block's later reads. Returns false on error.
+__device__ bool grid_barrier(Ctl* ctl, unsigned expected, volatile int* s_err, unsigned* reset)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* gen = &ctl->bar_gen;
+        volatile int* err = &ctl->err;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == expected - 1) {
+            // last arrival: every block is done with the pass, its work counter can restart
+            atomicExch(reset, 0u);
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const long long t0 = globaltimer_ns();
+            while (*gen == g) {
+                if (*err) break;
+                if (globaltimer_ns() - t0 > ctl->timeout_ns) {
+                    atomicCAS(&ctl->err, 0, (int)MPR_ERR_DEVICE_TIMEOUT);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        *s_err = *err;
+    }
+    __syncthreads();
+    return *s_err == 0;
+}
+
+// ---- the per-problem state machine (one thread, FP64) --------------------------------------
+
+__device__ void enter_run(Dyn& d, const Args& A)
+{
+    d.step = 0;
+    d.phase = A.equil > 0 ? kRunEquil : (A.samples > 0 ? kRunSample : kDone);
+    if (d.phase == kDone) {
+        atomicSub(&A.ctl->n_active, 1);
+        atomicExch(&A.ctl->changed, 1);
+    }
+}
+
+__device__ void start_probe(Dyn& d, const Args& A, double T)
+{
+    d.T = T;
+    d.esum = 0.0;
+    d.step = 0;
+    d.phase = A.n_eq > 0 ? kProbeEquil : kProbeMeasure;
+}
+
+// The next bisection probe, or the end of the tuning when the probes are used up.
+__device__ void next_mid(Dyn& d, const Args& A)
+{
+    if (d.np >= A.max_probes) {
+        d.T = exp(0.5 * (d.lo + d.hi));
+        d.status = MPR_ERR_TUNE_NO_CONVERGE;
+        enter_run(d, A);
+        return;
+    }
+    d.mid = 0.5 * (d.lo + d.hi);
+    d.kind = 2;
+    start_probe(d, A, exp(d.mid));
+}
+
+// A probe finished with mean bond energy e: one step of the bisection in log T.
+__device__ void probe_done(Dyn& d, const Args& A, double e_s, double e)
+{
+    const double tol = A.rel_tol * fabs(e_s);
+    if (d.kind == 0) {                       // T_lo
+        d.np = 1;
+        if (fabs(e - e_s) <= tol || e_s < e) { d.T = A.T_lo; enter_run(d, A); return; }
+        d.kind = 1;
+        start_probe(d, A, A.T_hi);
+        return;
+    }
+    if (d.kind == 1) {                       // T_hi
+        d.np = 2;
+        if (fabs(e - e_s) <= tol) { d.T = A.T_hi; enter_run(d, A); return; }
+        if (e_s > e) { d.T = A.T_hi; d.status = MPR_ERR_TUNE_NO_CONVERGE; enter_run(d, A); return; }
+        next_mid(d, A);
+        return;
+    }
+    d.np += 1;                               // bisection midpoint
+    if (fabs(e - e_s) <= tol) { enter_run(d, A); return; }
+    if (e < e_s) d.lo = d.mid; else d.hi = d.mid;
+    if (d.hi - d.lo < A.log_ratio) {
+        d.T = exp(0.5 * (d.lo + d.hi));
+        enter_run(d, A);
+        return;
+    }
+    next_mid(d, A);
+}
+
+__device__ void load_dyn(const Prob& P, Dyn& d)
+{
+    d.phase = __ldcg(&P.d.phase);
+    d.step = __ldcg(&P.d.step);
+    d.np = __ldcg(&P.d.np);
+    d.kind = __ldcg(&P.d.kind);
+    d.status = __ldcg(&P.d.status);
+    d.nsamples = __ldcg(&P.d.nsamples);
+    d.sweep = __ldcg(&P.d.sweep);
+    d.invTf = __ldcg(&P.d.invTf);
+    d.T = __ldcg(&P.d.T);
+    d.lo = __ldcg(&P.d.lo);
+    d.hi = __ldcg(&P.d.hi);
+    d.mid = __ldcg(&P.d.mid);
+    d.esum = __ldcg(&P.d.esum);
+    d.esamp = __ldcg(&P.d.esamp);
+    d.site_updates = __ldcg(&P.d.site_updates);
+}
+
+// The sweep's bond sum of problem P from its tile partials, by the whole block: thread t adds
+// tiles t, t + 256, ... and a shared-memory tree combines the 256 sums -- the same fixed order as
+// the single-problem reduction, so both paths give the same bits. Result valid in thread 0.
+template <typename E>
+__device__ double block_energy(const Prob& P, const Args& A, E* red)
+{
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const E* ep = static_cast<const E*>(A.epart) + P.tile_base;
+    E s = (E)0;
+    for (int i = tid; i < P.ntiles; i += 256) s += __ldcg(ep + i);
+    red[tid] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
+        __syncthreads();
+    }
+    return (double)red[0];
+}
+
+// After the last black tile of problem P in this sweep (one thread): the state machine, given the
+// sweep's raw bond sum when the sweep was measured.
+__device__ void bookkeeping(Prob& P, const Args& A, double raw)
+{
+    Dyn d;
+    load_dyn(P, d);
+    const int ph = d.phase;
+    double e = 0.0;
+    if (ph == kProbeMeasure || ph == kRunSample) e = -raw / P.Nb;
+    d.sweep += 1u;
+    d.site_updates += (unsigned long long)P.Np;
+    switch (ph) {
+    case kProbeEquil:
+        if (++d.step >= A.n_eq) { d.phase = kProbeMeasure; d.step = 0; }
+        break;
+    case kProbeMeasure:
+        d.esum += e;
+        if (++d.step >= A.n_meas) probe_done(d, A, P.e_s, d.esum / (double)A.n_meas);
+        break;
+    case kRunEquil:
+        if (++d.step >= A.equil) {
+            d.step = 0;
+            d.phase = A.samples > 0 ? kRunSample : kDone;
+            if (d.phase == kDone) {
+                atomicSub(&A.ctl->n_active, 1);
+                atomicExch(&A.ctl->changed, 1);
+            }
+        }
+        break;
+    case kRunSample:
+        d.esamp += e;
+        d.nsamples += 1;
+        if (++d.step >= A.samples) {
+            d.phase = kDone;
+            atomicSub(&A.ctl->n_active, 1);
+            atomicExch(&A.ctl->changed, 1);
+        }
+        break;
+    default:
+        break;
+    }
+    d.invTf = (float)(1.0 / d.T);
+    P.d = d;
+    P.tiles_done = 0u;
+}
+
+// ---- tiles ------------------------------------------------------------------------------------
+
+// Builds the sweep arguments of tile t (colour `colour`) and runs it. One function per variant,
+// not inlined, so every variant gets its own register allocation within the kernel's budget; the
+// arguments are a pointer and scalars, so nothing passes through local memory.
+template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
+__device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const Prob& P = A->prob[p];
+    SweepArgs a;
+    a.own = static_cast<char*>(A->ang) + (size_t)P.ang_off[colour] * sizeof(S);
+    a.other = static_cast<const char*>(A->ang) + (size_t)P.ang_off[colour ^ 1] * sizeof(S);
+    a.mbits = A->mb + P.mb_off[colour];
+    a.acc = A->acc ? A->acc + P.acc_off[colour] : nullptr;
+    a.acc_hi = A->acc_hi ? A->acc_hi + P.acc_off[colour] : nullptr;
+    a.acc_lo = A->acc_lo ? A->acc_lo + P.acc_off[colour] : nullptr;
+    a.epart = A->epart;
+    a.Lx = P.Lx;
+    a.Ly = P.Ly;
+    a.Lxh = P.Lxh;
+    a.pitch = P.pitch;
+    a.mpitch = P.mpitch;
+    a.colour = colour;
+    a.flags = A->energy_f32 ? kEnergyF32 : 0;
+    a.seed_lo = A->seed_lo;
+    a.seed_hi = A->seed_hi;
+    // state written by other blocks' bookkeeping: read at L2, not through this SM's L1
+    a.sweep = __ldcg(&P.d.sweep);
+    a.problem = (uint32_t)p;
+    a.q = A->q;
+    a.T = 0.0;
+    a.invT = 0.0;        // the FP32 tile uses qf and invTf only
+    a.qf = A->qf;
+    a.invTf = __ldcg(&P.d.invTf);
+    const int i = t - P.tile_base;
+    void* eslot = MEASURE ? static_cast<char*>(A->epart) + (size_t)t * (A->energy_f32 ? 4 : 8) : nullptr;
+    sweep_tile<S, R, MEASURE, SAMPLE, false>(a, i % P.ntx, i / P.ntx,
+                                             *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
+}
+
+template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
+__device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour)
+{
+    tile_body<S, R, TJ, MEASURE, SAMPLE>(A, t, p, colour);
+}
+
+// Tile t of problem p. The plain pass (no energy, no sampling: most passes) is inlined; the rarer
+// variants are calls.
+template <typename S, int R, int TJ>
+__device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p, int colour,
+                                        TileSmem<R, TJ>& sm)
+{
+    Prob& P = A->prob[p];
+    const int ph = __ldcg(&P.d.phase);
+    if (ph == kDone) return;
+    const bool measure = colour == 1 && (ph == kProbeMeasure || ph == kRunSample);
+    const bool sample = ph == kRunSample;
+    if (!measure && !sample) {
+        tile_body<S, R, TJ, false, 0>(A, t, p, colour);
+    } else if (measure && !sample) {
+        tile_fn<S, R, TJ, true, 0>(A, t, p, colour);
+    } else if (!measure) {
+        if (A->acc_kind == 0) tile_fn<S, R, TJ, false, 1>(A, t, p, colour);
+        else tile_fn<S, R, TJ, false, 2>(A, t, p, colour);
+    } else {
+        if (A->acc_kind == 0) tile_fn<S, R, TJ, true, 1>(A, t, p, colour);
+        else tile_fn<S, R, TJ, true, 2>(A, t, p, colour);
+    }
+    if (colour == 1) {
+        __shared__ int s_last;
+        __syncthreads();   // the tile's partial and spins are written before the arrival counts
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
+            s_last = atomicAdd(&P.tiles_done, 1u) == (unsigned)P.ntiles - 1u;
+            if (s_last) __threadfence();
+        }
+        __syncthreads();
+        if (s_last) {   // this block finished the problem's sweep: energy, then state machine
+            double raw = 0.0;
+            if (measure) {
+                raw = A->energy_f32 ? block_energy<float>(P, *A, reinterpret_cast<float*>(&sm.cs[0][0]))
+                                    : block_energy<double>(P, *A, reinterpret_cast<double*>(&sm.cs[0][0]));
+            }
+            if (threadIdx.x == 0 && threadIdx.y == 0) {
+                bookkeeping(P, *A, raw);
+                __threadfence();
+            }
+        }
+    }
+}
+
+// One colour pass over the active tile list: blocks take tiles from a shared counter (largest
+// tiles first, so uneven tiles and problems balance); the next index is fetched while the current
+// tile runs.
+template <typename S, int R, int TJ>
+__device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const int2* list, int n,
+                                            int colour, TileSmem<R, TJ>& sm, volatile int* s_k)
+{
+    if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
+    __syncthreads();
+    int k = *s_k;
+    while (k < n) {
+        __syncthreads();   // every thread has read s_k
+        if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
+        const int2 e = __ldcg(list + k);
+        do_tile<S, R, TJ>(A, e.x, e.y, colour, sm);
+        __syncthreads();
+        k = *s_k;
+    }
+}
+
+// Stable compaction of the active tile list (one block): drop the tiles of finished problems.
+__device__ void compact_list(const Args* __restrict__ A, const int2* src, int n, int2* dst, int* n_out,
+                             int* scan)
+{
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int per = (n + 255) / 256;
+    const int b = tid * per, e = min(n, b + per);
+    int cnt = 0;
+    for (int k = b; k < e; ++k) cnt += __ldcg(&A->prob[__ldcg(src + k).y].d.phase) != kDone;
+    scan[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int i = 0; i < 256; ++i) {
+            const int c = scan[i];
+            scan[i] = run;
+            run += c;
+        }
+        *n_out = run;
+    }
+    __syncthreads();
+    int o = scan[tid];
+    for (int k = b; k < e; ++k) {
+        const int2 t = __ldcg(src + k);
+        if (__ldcg(&A->prob[t.y].d.phase) != kDone) dst[o++] = t;
+    }
+    __threadfence();
+    __syncthreads();
+}
+
+template <typename S, int R, int TJ>
+__global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ A)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    TileSmem<R, TJ>& sm = *reinterpret_cast<TileSmem<R, TJ>*>(dsm);
+    __shared__ int s_err, s_k, s_active, s_changed, s_sel, s_n;
+    __shared__ int s_scan[256];
+    Ctl* ctl = A->ctl;
+    const unsigned expected = gridDim.x + (unsigned)ctl->bar_extra;
+    const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
+    if (t0) {
+        s_sel = __ldcg(&ctl->list_sel);
+        s_n = __ldcg(&ctl->n_list);
+    }
+    __syncthreads();
+    for (int it = 0; it < A->max_iters; ++it) {
+        const int2* list = A->lists + (size_t)s_sel * A->ntiles;
+        const int n = s_n;
+        colour_pass<S, R, TJ>(A, list, n, 0, sm, &s_k);
+        if (!grid_barrier(ctl, expected, &s_err, &ctl->work[0])) return;
+        colour_pass<S, R, TJ>(A, list, n, 1, sm, &s_k);
+        if (!grid_barrier(ctl, expected, &s_err, &ctl->work[1])) return;
+        if (t0) {
+            s_active = __ldcg(&ctl->n_active);
+            s_changed = __ldcg(&ctl->changed);
+            if (blockIdx.x == 0) ctl->iters = it + 1;
+        }
+        __syncthreads();
+        if (s_active <= 0) return;
+        if (s_changed) {   // a problem finished in this sweep: shrink the tile list
+            if (blockIdx.x == 0) {
+                const int sel = s_sel;
+                compact_list(A, list, n, A->lists + (size_t)(sel ^ 1) * A->ntiles, &ctl->n_list, s_scan);
+                if (t0) {
+                    atomicExch(&ctl->list_sel, sel ^ 1);
+                    atomicExch(&ctl->changed, 0);
+                    __threadfence();
+                }
+            }
+            if (!grid_barrier(ctl, expected, &s_err, &ctl->work[0])) return;
+            if (t0) {
+                s_sel = __ldcg(&ctl->list_sel);
+                s_n = __ldcg(&ctl->n_list);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---- graph mode: one launch of a CUDA graph whose while-loop node repeats a red and a black
+// pass kernel and the finish kernel (mpr_batch.cu) on the device until every problem is done. Each pass kernel runs one tile per block (the
+// hardware scheduler overlaps many blocks, hiding each tile's load latency); the finish kernel
+// shrinks the tile list and sets the loop condition. No grid barrier, no spin wait.
+
+template <typename S, int R, int TJ>
+__global__ void __launch_bounds__(256, tile_min_blocks<R>()) pass_kernel(const Args* __restrict__ A, int colour)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const Ctl* ctl = A->ctl;
+    const int k = blockIdx.x;
+    if (k >= __ldcg(&ctl->n_list)) return;
+    const int2 e = __ldcg(A->lists + (size_t)__ldcg(&ctl->list_sel) * A->ntiles + k);
+    do_tile<S, R, TJ>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R, TJ>*>(dsm));
+}
+
+
+// The kernels of storage type S for tile shape s (kShape).
+template <typename S, int R, int TJ>
+Kernels entry()
+{
+    return Kernels{reinterpret_cast<const void*>(&pass_kernel<S, R, TJ>),
+                   reinterpret_cast<const void*>(&batch_kernel<S, R, TJ>), sizeof(TileSmem<R, TJ>)};
+}
+
+template <typename S>
+Kernels table(int s)
+{
+    switch (s) {
+    case 0: return entry<S, 1, 128>();
+    case 1: return entry<S, 2, 128>();
+    case 2: return entry<S, 4, 128>();
+    case 3: return entry<S, 1, 64>();
+    case 4: return entry<S, 2, 64>();
+    default: return Kernels{nullptr, nullptr, 0};
+    }
+}
+
+}  // namespace
+}  // namespace batch
+}  // namespace mpr

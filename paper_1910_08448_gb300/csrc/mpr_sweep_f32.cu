@@ -1,15 +1,16 @@
 // mpr_sweep_f32.cu -- single-problem colour half-sweep for the FP32 function setting: one launch
 // per colour pass over tiles of mpr_tile_f32.cuh. Two kernels with the same per-site arithmetic,
 // so their results are equal bit for bit:
-//  - sweep_f32_kernel: one 128 x 16 tile per block, 4 blocks per SM, staging with ordinary loads;
-//    the hardware block scheduler overlaps one block's loads with other blocks' work, and the
-//    many small tiles leave little imbalance between SMs at the end of a pass.
-//  - sweep_f32_tma_kernel: persistent blocks (2 per SM) walk 128 x 32 tiles t = blockIdx.x,
+//  - sweep_f32_kernel: one 128 x 32 tile per block, 3 blocks per SM, staging with ordinary loads;
+//    the hardware block scheduler overlaps one block's loads with other blocks' work, and blocks
+//    that start and end at different times keep the SM's pipes evenly loaded.
+//  - sweep_f32_tma_kernel: persistent blocks (3 per SM) walk 128 x 32 tiles t = blockIdx.x,
 //    blockIdx.x + gridDim.x, ...; while a block updates tile t, the TMA unit copies the next
 //    tile's three boxes (other colour with halo, own values, own frozen bits) into shared memory,
-//    completing on one mbarrier, so the staging step is pure sin/cos work and the taller tile
-//    halves the halo rows per site. Faster on large lattices; on smaller ones the coarser tiles
-//    divide less evenly over the SMs. The handle picks one by timing both (mpr_set_sweep_kernel).
+//    completing on one mbarrier, so the staging step is pure sin/cos work. Blocks that walk equal
+//    tiles stay in step with each other (all convert, then all update), and the static tile
+//    split leaves part of the last round idle. The handle picks the faster kernel by timing both
+//    (mpr_set_sweep_kernel).
 #include "mpr.h"
 #include "mpr_tile_f32.cuh"
 #include "mpr_tma.cuh"
@@ -21,11 +22,11 @@ namespace {
 
 using namespace f32;
 
-constexpr int kRows = 2;      // rows per warp of the one-tile-per-block kernel
+constexpr int kRows = 4;      // rows per warp of the one-tile-per-block kernel
 constexpr int kTmaRows = 4;   // rows per warp of the TMA kernel's tiles
 
 template <typename S, int R, bool MEASURE, int SAMPLE>
-__global__ void __launch_bounds__(256, 4) sweep_f32_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, tile_min_blocks<R>()) sweep_f32_kernel(const SweepArgs a)
 {
     __shared__ __align__(16) TileSmem<R> sm;
     // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(256, 4) sweep_f32_kernel(const SweepArgs a)
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    sweep_tile<S, R, MEASURE, SAMPLE, true>(a, b % ntx, b / ntx, sm, eslot);
+    sweep_tile<S, R, MEASURE, SAMPLE, true, true>(a, b % ntx, b / ntx, sm, eslot);
 }
 
 // Shared memory of the TMA kernel: the boxes the TMA unit writes (other colour rows y0-1 ..
@@ -78,7 +79,7 @@ __device__ __forceinline__ void convert(const SweepArgs& a, const TmaSmem<S, R>&
 // Plain passes only (no fused energy, no sampling): the handle runs those passes with
 // sweep_f32_kernel, whose per-tile energy partials it reduces.
 template <typename S, int R>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     sweep_f32_tma_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap m_other,
                          const __grid_constant__ CUtensorMap m_own,
                          const __grid_constant__ CUtensorMap m_mask)
@@ -182,12 +183,22 @@ cudaError_t go_tma(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Launched as a programmatic dependent launch: while the previous pass's last blocks finish, this
+// pass's blocks are scheduled and load their own rows (see sweep_tile).
 template <typename S, bool MEASURE, int SAMPLE>
 cudaError_t go(const SweepArgs& a, cudaStream_t st)
 {
-    const dim3 grid(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>()));
-    sweep_f32_kernel<S, kRows, MEASURE, SAMPLE><<<grid, dim3(32, kWarps), 0, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>()));
+    cfg.blockDim = dim3(32, kWarps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_f32_kernel<S, kRows, MEASURE, SAMPLE>, a);
 }
 
 template <typename S>

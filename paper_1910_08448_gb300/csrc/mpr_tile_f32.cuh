@@ -4,10 +4,12 @@
 // Used by the single-problem kernel (one tile per block) and the batched persistent kernel
 // (many tiles of many problems per block).
 //
-// Tile: 128 half-lattice columns x (8 warps x R rows). A thread owns 4 consecutive columns of a
-// row (two same-colour site pairs -> two Philox calls), loaded and stored as one vector. The other
-// colour's tile and its one-site halo are staged in shared memory as unit vectors
-// (cos q*phi, sin q*phi), computed once per site and read by its four neighbours.
+// Tile: TJ half-lattice columns (128, or 64 for narrow lattices) x TY rows. A thread owns 4
+// consecutive columns of a row (two same-colour site pairs -> two Philox calls), loaded and stored
+// as one vector; a warp step covers one 128-column row or two 64-column rows, and each thread
+// handles R rows, so TY = 8 warps x (128 / TJ) x R. The other colour's tile and its one-site halo
+// are staged in shared memory as unit vectors (cos q*phi, sin q*phi), computed once per site and
+// read by its four neighbours.
 #pragma once
 
 #include "mpr_device.cuh"
@@ -16,8 +18,15 @@
 namespace mpr {
 namespace f32 {
 
-constexpr int kTJ = 128;     // half-lattice columns per tile
+constexpr int kTJ = 128;     // half-lattice columns per tile (single-problem kernels)
 constexpr int kWarps = 8;    // 256 threads, blockDim = (32, 8)
+
+// Lanes of a warp per tile row (TJ / 4) and tile rows per warp step.
+template <int TJ> struct Lanes {
+    static_assert(TJ == 128 || TJ == 64, "tile width");
+    static constexpr int kPerRow = TJ / 4;
+    static constexpr int kRows = 32 / kPerRow;
+};
 
 // Twice atan2(y, x) modulo 2*pi, in FP32, as an angle in [-pi, pi] (the over-relaxation needs the
 // doubled angle only modulo 2*pi). Reduce to a = min(|x|,|y|)/max(|x|,|y|) in [0, 1] and evaluate
@@ -84,18 +93,24 @@ __device__ __forceinline__ void store4(S* p, const Pack4<S>& in)
     }
 }
 
+template <int R, int TJ = kTJ> __host__ __device__ constexpr int tile_rows()
+{
+    return kWarps * Lanes<TJ>::kRows * R;
+}
+
 // Shared tile of the other colour as structure of arrays: column j of the tile at index
-// j - j0 + 4 (halo columns at 3 and kTJ + 4), so a lane's four interior columns form one aligned
+// j - j0 + 4 (halo columns at 3 and TJ + 4), so a lane's four interior columns form one aligned
 // 16-byte vector and a warp's vector accesses touch consecutive banks.
-constexpr int kSW = kTJ + 8;
-template <int R> struct TileSmem {
-    float cs[kWarps * R + 2][kSW];
-    float sn[kWarps * R + 2][kSW];
+template <int R, int TJ = kTJ> struct TileSmem {
+    float cs[tile_rows<R, TJ>() + 2][TJ + 8];
+    float sn[tile_rows<R, TJ>() + 2][TJ + 8];
     double wsum_d[kWarps];
     float wsum_f[kWarps];
 };
 
-template <int R> __host__ __device__ constexpr int tile_rows() { return kWarps * R; }
+// Resident blocks per SM the tile kernels are compiled for: 4 (64 registers) for tiles of up to
+// 2 rows per warp, 3 (85 registers) for 4 rows per warp, whose row loop holds more values.
+template <int R> __host__ __device__ constexpr int tile_min_blocks() { return R >= 4 ? 3 : 4; }
 
 // 2^x on the MUFU (hand-written PTX: ex2.approx.ftz.f32)
 __device__ __forceinline__ float ex2_approx(float x)
@@ -107,14 +122,14 @@ __device__ __forceinline__ float ex2_approx(float x)
 
 // Converts one staged row r (tile row y = y0 - 1 + r, parity ob of its columns) of the other
 // colour to unit vectors (cos q*phi, sin q*phi) in sm: the thread's four columns from st, the halo
-// column j0 - 1 (lane 0) or j0 + TJ (lane 1) from halo. Entries outside the lattice become (0, 0)
-// (open boundaries); CHECK = false when the caller knows every entry exists.
-template <typename S, int R, bool CHECK>
+// column j0 - 1 (first lane of the row) or j0 + TJ (second lane) from halo. Entries outside the
+// lattice become (0, 0) (open boundaries); CHECK = false when the caller knows every entry exists.
+template <typename S, int R, bool CHECK, int TJ>
 __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j0, int jb, int lj,
                                          int ob, float q, const Pack4<S>& st, S halo,
-                                         TileSmem<R>& sm)
+                                         TileSmem<R, TJ>& sm)
 {
-    const int lane = threadIdx.x;
+    const int lc = threadIdx.x % Lanes<TJ>::kPerRow;   // lane within the row
     const bool row_ok = !CHECK || (y >= 0 && y < a.Ly);
     float vc[4], vs[4];
 #pragma unroll
@@ -126,9 +141,9 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
     }
     *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
     *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-    if (lane < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index kTJ + 4)
-        const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
-        const int cc = lane == 0 ? 3 : kTJ + 4;
+    if (lc < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index TJ + 4)
+        const int j = lc == 0 ? j0 - 1 : j0 + TJ;
+        const int cc = lc == 0 ? 3 : TJ + 4;
         float hc = 0.0f, hs = 0.0f;
         if (!CHECK || (row_ok && j >= 0 && 2 * j + ob < a.Lx))
             __sincosf(q * load_as<float>(halo), &hs, &hc);
@@ -139,23 +154,25 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
 
 // Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile from global
 // memory as unit vectors. All loads are issued before the sin/cos work.
-template <typename S, int R, bool CHECK>
+template <typename S, int R, bool CHECK, int TJ>
 __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ other, int y0,
-                                      int j0, int jb, int lj, int cb, float q, TileSmem<R>& sm)
+                                      int j0, int jb, int lj, int cb, float q, TileSmem<R, TJ>& sm)
 {
-    constexpr int TY = kWarps * R;
-    constexpr int NR = (TY + 2 + kWarps - 1) / kWarps;   // staged rows per warp
-    const int lane = threadIdx.x, warp = threadIdx.y;
+    constexpr int TY = tile_rows<R, TJ>();
+    constexpr int HW = Lanes<TJ>::kRows;
+    constexpr int NR = (TY + 2 + kWarps * HW - 1) / (kWarps * HW);   // staged rows per thread
+    const int warp = threadIdx.y;
+    const int lc = threadIdx.x % Lanes<TJ>::kPerRow, lr = threadIdx.x / Lanes<TJ>::kPerRow;
     Pack4<S> st[NR];
     S halo[NR];
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        const int r = warp + i * kWarps;
+        const int r = (warp + i * kWarps) * HW + lr;
         const int y = y0 - 1 + r;
         if (r < TY + 2 && (!CHECK || (y >= 0 && y < a.Ly))) {
             load4(other + (size_t)y * a.pitch + jb, st[i]);
-            if (lane < 2) {
-                const int j = lane == 0 ? j0 - 1 : j0 + kTJ;
+            if (lc < 2) {
+                const int j = lc == 0 ? j0 - 1 : j0 + TJ;
                 if (!CHECK || (j >= 0 && 2 * j + ((y + cb) & 1) < a.Lx))
                     halo[i] = other[(size_t)y * a.pitch + j];
             }
@@ -163,7 +180,7 @@ __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ 
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        const int r = warp + i * kWarps;
+        const int r = (warp + i * kWarps) * HW + lr;
         if (r >= TY + 2) break;
         const int y = y0 - 1 + r;
         unit_row<S, R, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st[i], halo[i], sm);
@@ -191,9 +208,9 @@ template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, fl
 // existing (black) sites to e_d or e_f. SCHED: Philox words from the precomputed schedule a.ph
 // (a kernel parameter) instead of the seed. OPAR: the row's column offset o = (y + colour) & 1
 // when the caller knows it at compile time (0 or 1), else -1.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, int TJ>
 __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
-                                           Pack4<S>& pk, uint32_t bits, const TileSmem<R>& sm,
+                                           Pack4<S>& pk, uint32_t bits, const TileSmem<R, TJ>& sm,
                                            double& e_d, float& e_f)
 {
     const int c = a.colour;
@@ -316,9 +333,9 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
 
 // The tile's energy partial: warp shuffles, then the warps in order, written by thread (0, 0) to
 // *eslot (double, or float with kEnergyF32). Contains a block barrier.
-template <int R>
+template <int R, int TJ>
 __device__ __forceinline__ void tile_energy(const SweepArgs& a, double e_d, float e_f,
-                                            TileSmem<R>& sm, void* eslot)
+                                            TileSmem<R, TJ>& sm, void* eslot)
 {
     const int lane = threadIdx.x, warp = threadIdx.y;
 #pragma unroll
@@ -344,17 +361,18 @@ __device__ __forceinline__ void tile_energy(const SweepArgs& a, double e_d, floa
     }
 }
 
-// Row order within a warp. With an even number R of rows per warp (and tile origins at even rows)
-// row rr of a warp has o = (rr + colour) & 1, so visiting rr = i ^ colour makes o = i & 1 a
-// compile-time constant of the unrolled loop over i. Odd R keeps the natural order, o at run time.
+// Row order of a thread's R rows. With even R (and tile origins at even rows) the thread's rows
+// start at an even tile row, so its row rr has o = (rr + colour) & 1, and visiting rr = i ^ colour
+// makes o = i & 1 a compile-time constant of the unrolled loop over i. Odd R keeps the natural
+// order, o at run time.
 template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R % 2 == 0) ? (i ^ c) : i; }
 
 // update_row of the i-th row in the order row_of(), with o fixed at compile time for even R (the
 // branch on i & 1 disappears when the caller's loop over i is unrolled).
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int TJ>
 __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
                                              int lj, Pack4<S>& pk, uint32_t bits,
-                                             const TileSmem<R>& sm, double& e_d, float& e_f)
+                                             const TileSmem<R, TJ>& sm, double& e_d, float& e_f)
 {
     if constexpr (R % 2 == 0) {
         if (i & 1) update_row<S, R, MEASURE, SAMPLE, SCHED, 1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
@@ -367,26 +385,34 @@ __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, i
 // One tile (tile column tx, tile row ty) of colour a.colour, staged from global memory. With
 // MEASURE (black pass) the tile's sum of u_b . h_b over its existing black sites is written to
 // *eslot. Begins with a block barrier, so a block may call it for several tiles in a row.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED>
-__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R>& sm,
+// PDL (programmatic dependent launch, one tile per block): the block reads its own colour's values
+// and bits, then waits for the previous kernel (the other colour's pass), then lets the next
+// kernel in the stream start launching. The own colour was last written two passes back, which
+// has completed: the previous pass's blocks released this pass only after their own wait.
+// Everything the previous pass may write (the other colour, accumulators, energy partials) is
+// touched only after the wait.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false, int TJ = kTJ>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
-    constexpr int TY = kWarps * R;
+    constexpr int TY = tile_rows<R, TJ>();
     const int c = a.colour, cb = c ^ 1;
-    const int j0 = tx * kTJ;
+    const int j0 = tx * TJ;
     const int y0 = ty * TY;
-    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int warp = threadIdx.y;
+    const int lc = threadIdx.x % Lanes<TJ>::kPerRow, lr = threadIdx.x / Lanes<TJ>::kPerRow;
+    const int row0 = (warp * Lanes<TJ>::kRows + lr) * R;   // first of this thread's R tile rows
     const S* __restrict__ other = static_cast<const S*>(a.other);
     const S* __restrict__ own = static_cast<const S*>(a.own);
-    const int jb = j0 + 4 * lane;             // first of this thread's 4 columns
-    const int lj = 4 * lane;
+    const int lj = 4 * lc;
+    const int jb = j0 + lj;                   // first of this thread's 4 columns
 
     // ---- own rows: values and frozen bits, loaded before the staging so their latency overlaps
     Pack4<S> mine[R];   // in the order row_of()
     uint32_t bits[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-        const int y = y0 + warp * R + row_of<R>(i, c);
+        const int y = y0 + row0 + row_of<R>(i, c);
         bits[i] = 0xFu;
         if (y < a.Ly) {
             load4(own + (size_t)y * a.pitch + jb, mine[i]);
@@ -394,10 +420,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         }
     }
 
+    if (PDL) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous pass is complete
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
     __syncthreads();   // the previous tile's readers are done with sm
     // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
     // lies inside the lattice (nearly all) skip the per-entry bounds checks.
-    const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
+    const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + TJ) + 1 < a.Lx;
     if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
     else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
     __syncthreads();
@@ -406,12 +436,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
     float e_f = 0.0f;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-        const int ly = warp * R + row_of<R>(i, c);
+        const int ly = row0 + row_of<R>(i, c);
         const int y = y0 + ly;
         if (y < a.Ly)
             update_row_i<S, R, MEASURE, SAMPLE, SCHED>(i, a, y, ly, jb, lj, mine[i], bits[i], sm, e_d, e_f);
     }
-    if (MEASURE) tile_energy<R>(a, e_d, e_f, sm, eslot);
+    if (MEASURE) tile_energy(a, e_d, e_f, sm, eslot);
 }
 
 }  // namespace f32

@@ -45,6 +45,13 @@ def test_library_is_sm103a_build():
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH
 
 
+def test_mufu_probe_is_built(lib):
+    # the special-function throughput probe that bench.py runs for its roofline
+    from paper_1910_08448_gb300 import _build
+
+    assert os.path.isfile(_build.PROBE) and os.access(_build.PROBE, os.X_OK)
+
+
 def test_status_strings(lib):
     import paper_1910_08448_gb300 as mpr
 

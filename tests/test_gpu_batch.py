@@ -163,11 +163,13 @@ def test_batch_tuning_matches_single_handle(mpr):
 def test_batch_launch_shape_and_graph_do_not_change_results(mpr):
     probs = _problems(base=100)
     states = []
-    for rows, bps, mode in [(1, 1, 0), (2, 0, 2), (4, 2, 1), (2, 1, 0), (4, 0, 2), (1, 0, 2)]:
+    shapes = [(8, 128, 1, 0), (16, 128, 0, 2), (32, 128, 2, 1), (16, 128, 1, 0), (32, 128, 0, 2),
+              (8, 128, 0, 2), (16, 64, 0, 2), (32, 64, 1, 0), (32, 64, 0, 2), (16, 64, 2, 1)]
+    for rows, cols, bps, mode in shapes:
         b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "HDS", seed=3,
                                  acc="kahan")
         try:
-            mpr.mpr_batch_set_launch(b, rows, bps, mode)
+            mpr.mpr_batch_set_launch(b, rows, cols, bps, mode)
             mpr.mpr_batch_fill(b, 15, 5, T=np.linspace(0.1, 1.0, len(probs)))
             states.append([mpr.mpr_batch_get_state(b, i)[0] for i in range(len(probs))]
                           + [mpr.mpr_batch_predict(b, i) for i in range(len(probs))])
@@ -183,8 +185,9 @@ def test_batch_autotune_keeps_state(mpr):
     b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "SDS", seed=1)
     try:
         before = [mpr.mpr_batch_get_state(b, i) for i in range(len(probs))]
-        rows, bps, mode = mpr.mpr_batch_autotune(b, 5)
-        assert rows in (1, 2, 4) and mode in (0, 2) and (bps >= 1 or mode == 2)
+        rows, cols, bps, mode = mpr.mpr_batch_autotune(b, 5)
+        assert (rows, cols) in ((8, 128), (16, 128), (32, 128), (16, 64), (32, 64))
+        assert mode in (0, 2) and (bps >= 1 or mode == 2)
         after = [mpr.mpr_batch_get_state(b, i) for i in range(len(probs))]
         for (a, sa), (c, sc) in zip(before, after):
             assert np.array_equal(a, c) and sa == sc
@@ -198,7 +201,7 @@ def test_batch_barrier_timeout_is_reported(mpr):
     probs = _problems()[:3]
     b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "SDS")
     try:
-        mpr.mpr_batch_set_launch(b, 2, 0, 0)   # the persistent kernel is the one with barriers
+        mpr.mpr_batch_set_launch(b, 16, 128, 0, 0)   # the persistent kernel is the one with barriers
         mpr.mpr_batch_inject_barrier_fault(b, 1, 0.05)
         with pytest.raises(mpr.MPRError) as e:
             mpr.mpr_batch_fill(b, 3, 1, T=np.full(3, 0.5))
