@@ -37,7 +37,8 @@ struct Prob {
     double Nb;                  // bonds
     double e_s;                 // sample energy
     unsigned tiles_done;        // black tiles finished in this sweep (arrival counter)
-    unsigned pad_;
+    int tail64;                 // 128-column tiles: the last tile column is 64 wide (it holds
+                                // at most 64 columns), run with the 64-column tile code
     Dyn d;
 };
 

@@ -224,7 +224,8 @@ __device__ void bookkeeping(Prob& P, const Args& A, double raw)
 // not inlined, so every variant gets its own register allocation within the kernel's budget; the
 // arguments are a pointer and scalars, so nothing passes through local memory.
 template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
-__device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour)
+__device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour,
+                                          int tx, int ty)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const Prob& P = A->prob[p];
@@ -253,16 +254,34 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
     a.invT = 0.0;        // the FP32 tile uses qf and invTf only
     a.qf = A->qf;
     a.invTf = __ldcg(&P.d.invTf);
-    const int i = t - P.tile_base;
     void* eslot = MEASURE ? static_cast<char*>(A->epart) + (size_t)t * (A->energy_f32 ? 4 : 8) : nullptr;
-    sweep_tile<S, R, MEASURE, SAMPLE, false>(a, i % P.ntx, i / P.ntx,
+    sweep_tile<S, R, MEASURE, SAMPLE, false>(a, tx, ty,
                                              *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
 }
 
 template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
-__device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour)
+__device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour, int tx,
+                                     int ty)
 {
-    tile_body<S, R, TJ, MEASURE, SAMPLE>(A, t, p, colour);
+    tile_body<S, R, TJ, MEASURE, SAMPLE>(A, t, p, colour, tx, ty);
+}
+
+// The variant of a tile of shape (R, TJ) for this pass: plain inlined, the others as calls.
+template <typename S, int R, int TJ>
+__device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, int p, int colour,
+                                             int tx, int ty, bool measure, bool sample)
+{
+    if (!measure && !sample) {
+        tile_body<S, R, TJ, false, 0>(A, t, p, colour, tx, ty);
+    } else if (measure && !sample) {
+        tile_fn<S, R, TJ, true, 0>(A, t, p, colour, tx, ty);
+    } else if (!measure) {
+        if (A->acc_kind == 0) tile_fn<S, R, TJ, false, 1>(A, t, p, colour, tx, ty);
+        else tile_fn<S, R, TJ, false, 2>(A, t, p, colour, tx, ty);
+    } else {
+        if (A->acc_kind == 0) tile_fn<S, R, TJ, true, 1>(A, t, p, colour, tx, ty);
+        else tile_fn<S, R, TJ, true, 2>(A, t, p, colour, tx, ty);
+    }
 }
 
 // Tile t of problem p. The plain pass (no energy, no sampling: most passes) is inlined; the rarer
@@ -276,16 +295,19 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p
     if (ph == kDone) return;
     const bool measure = colour == 1 && (ph == kProbeMeasure || ph == kRunSample);
     const bool sample = ph == kRunSample;
-    if (!measure && !sample) {
-        tile_body<S, R, TJ, false, 0>(A, t, p, colour);
-    } else if (measure && !sample) {
-        tile_fn<S, R, TJ, true, 0>(A, t, p, colour);
-    } else if (!measure) {
-        if (A->acc_kind == 0) tile_fn<S, R, TJ, false, 1>(A, t, p, colour);
-        else tile_fn<S, R, TJ, false, 2>(A, t, p, colour);
+    const int i = t - P.tile_base;
+    const int tx = i % P.ntx, ty = i / P.ntx;
+    // 128-column tiles with an even row count per thread: a problem whose last tile column holds
+    // at most 64 columns runs that column with the 64-column code of the same height (tile column
+    // 2 tx in 64-column units), wasting half as much of the tile
+    constexpr bool kTail = TJ == 128 && R % 2 == 0;
+    if constexpr (kTail) {
+        if (P.tail64 && tx == P.ntx - 1)
+            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample);
+        else
+            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample);
     } else {
-        if (A->acc_kind == 0) tile_fn<S, R, TJ, true, 1>(A, t, p, colour);
-        else tile_fn<S, R, TJ, true, 2>(A, t, p, colour);
+        tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample);
     }
     if (colour == 1) {
         __shared__ int s_last;

@@ -1,7 +1,7 @@
 // mpr_sweep_f32.cu -- single-problem colour half-sweep for the FP32 function setting: one launch
 // per colour pass over tiles of mpr_tile_f32.cuh. Two kernels with the same per-site arithmetic,
 // so their results are equal bit for bit:
-//  - sweep_f32_kernel: one 128 x 32 tile per block, 3 blocks per SM, staging with ordinary loads;
+//  - sweep_f32_kernel: one 128 x 32 tile per block, 4 blocks per SM, staging with ordinary loads;
 //    the hardware block scheduler overlaps one block's loads with other blocks' work, and blocks
 //    that start and end at different times keep the SM's pipes evenly loaded.
 //  - sweep_f32_tma_kernel: persistent blocks (3 per SM) walk 128 x 32 tiles t = blockIdx.x,
@@ -25,17 +25,29 @@ using namespace f32;
 constexpr int kRows = 4;      // rows per warp of the one-tile-per-block kernel
 constexpr int kTmaRows = 4;   // rows per warp of the TMA kernel's tiles
 
+// Plain passes (no energy, no sampling: nearly all) compile for 4 resident blocks per SM (64
+// registers, no spills with 4-row tiles); the energy and sampling variants for tile_min_blocks.
 template <typename S, int R, bool MEASURE, int SAMPLE>
-__global__ void __launch_bounds__(256, tile_min_blocks<R>()) sweep_f32_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, (MEASURE || SAMPLE) ? tile_min_blocks<R>() : 4)
+    sweep_f32_kernel(const SweepArgs a)
 {
+    static_assert(R % 2 == 0, "the 64-column tail tile has R / 2 rows per thread");
     __shared__ __align__(16) TileSmem<R> sm;
     // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
     const int b = blockIdx.x;
     const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    const int tx = b % ntx, ty = b / ntx;
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    sweep_tile<S, R, MEASURE, SAMPLE, true, true>(a, b % ntx, b / ntx, sm, eslot);
+    // a last tile column of at most 64 columns runs as a 64-column tile of the same height (tile
+    // column 2 tx in 64-column units), as the batched kernels do: the energy partials, and so the
+    // energies, stay bit-identical between the two paths
+    if (tx == ntx - 1 && a.Lxh - tx * kTJ <= 64)
+        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true>(
+            a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
+    else
+        sweep_tile<S, R, MEASURE, SAMPLE, true, true>(a, tx, ty, sm, eslot);
 }
 
 // Shared memory of the TMA kernel: the boxes the TMA unit writes (other colour rows y0-1 ..
