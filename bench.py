@@ -169,10 +169,18 @@ class ClockSampler:
 # the measured arm
 # ------------------------------------------------------------------------------------------------
 
-def sweep_kernel_id() -> str:
-    """Hash of the sweep kernel's sources: ties stored ncu counters to the code they came from."""
+KERNEL_SOURCES = {
+    "mpr::sweep_f32_kernel": ("mpr_tile_f32.cuh", "mpr_sweep_f32.cu", "mpr_device.cuh"),
+    "mpr::sweep_f32_tma_kernel": ("mpr_tile_f32.cuh", "mpr_sweep_tma.cu", "mpr_tma.cuh",
+                                  "mpr_device.cuh"),
+    "mpr::sweep_kernel": ("mpr_sweep.cu", "mpr_device.cuh"),
+}
+
+
+def sweep_kernel_id(kernel: str = "mpr::sweep_f32_kernel") -> str:
+    """Hash of a sweep kernel's sources: ties stored ncu counters to the code they came from."""
     h = hashlib.sha256()
-    for f in ("mpr_tile_f32.cuh", "mpr_sweep_f32.cu", "mpr_device.cuh", "mpr_tma.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1910_08448_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -305,8 +313,8 @@ def run_mine(args, dist: Dist):
     mufu_launch = t_mufu * r_sc
     mufu_peak = r_sc
     t_hbm = bytes_launch / (hbm_gbs * 1e9)
-    kid = sweep_kernel_id()
     kname = SWEEP_KERNELS[infos[-1]["sweep_kernel"]]
+    kid = sweep_kernel_id(kname)
     workload = f"L{L}_p{p}_{args.setup}"
     traffic = stored_traffic(kid, kname, workload)
     if t_hbm >= t_mufu:

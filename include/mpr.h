@@ -158,6 +158,14 @@ mpr_status mpr_set_profiling(mpr_handle h, int on);
  * stays across mpr_set_options while it remains available; an automatic choice is redone. */
 mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind);
 
+/* Test hook for the bounded wait of the TMA kernel: in the next pass that runs with kind 1, block
+ * 0 issues no copy for its first tile, so its mbarrier wait runs out after timeout_s (0 < timeout_s
+ * <= 10); the block records MPR_ERR_DEVICE_TIMEOUT and returns, the other blocks finish, nothing
+ * faults or hangs, and the call that synchronises next (e.g. mpr_run) returns
+ * MPR_ERR_DEVICE_TIMEOUT. That pass leaves the tiles of block 0 unchanged (the chain deviates);
+ * the handle stays usable. INVALID_ARG if the handle cannot run kind 1. */
+mpr_status mpr_inject_tma_stall(mpr_handle h, double timeout_s);
+
 /* State access for checkpoints and tests: angles as Lx*Ly doubles, row-major, host memory.
  * mpr_set_state writes the prediction sites only (rounded to the storage type), leaves the
  * frozen sites as mapped, and sets the next sweep index. */

@@ -96,6 +96,7 @@ def load():
             "mpr_get_info": ([H, P(mpr_info)], i),
             "mpr_set_profiling": ([H, i], i),
             "mpr_set_sweep_kernel": ([H, i], i),
+            "mpr_inject_tma_stall": ([H, d], i),
             "mpr_get_state": ([H, vp, P(u32)], i),
             "mpr_set_state": ([H, vp, u32], i),
             "mpr_philox4x32_10_dev": ([vp, vp, i, u64, vp], i),
@@ -129,7 +130,7 @@ def exported_symbols():
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_run", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
-            "mpr_set_sweep_kernel",
+            "mpr_set_sweep_kernel", "mpr_inject_tma_stall",
             "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error",
             "mpr_batch_create", "mpr_batch_destroy", "mpr_batch_set_stream",
             "mpr_batch_set_tuning", "mpr_batch_set_launch", "mpr_batch_autotune",
@@ -271,6 +272,11 @@ def mpr_set_profiling(h, on: bool = True):
 def mpr_set_sweep_kernel(h, kind: int):
     """FP32-function sweep kernel: -1 automatic (default), 0 one tile per block, 1 TMA-fed."""
     _check(load().mpr_set_sweep_kernel(h, int(kind)))
+
+
+def mpr_inject_tma_stall(h, timeout_s: float = 0.05):
+    """Test hook: the next TMA-kernel pass has a wait that runs out (see include/mpr.h)."""
+    _check(load().mpr_inject_tma_stall(h, float(timeout_s)))
 
 
 def mpr_get_state(h):

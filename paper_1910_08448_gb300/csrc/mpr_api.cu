@@ -124,6 +124,7 @@ struct mpr_ctx {
     TmaMaps tma{};
     int nsm = 0;                         // SMs of the device
     int sweep_force = -1;                // mpr_set_sweep_kernel: -1 automatic, 0, 1
+    long long stall_ns = 0;              // mpr_inject_tma_stall: wait limit of the next TMA pass
     int sweep_kind = -1;                 // automatic choice (-1 until made)
     cudaEvent_t cal[4] = {nullptr, nullptr, nullptr, nullptr};   // timing of the choice
 };
@@ -396,6 +397,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.epart = h->part;
     a.err = dev_err(h);
     a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds
+    a.stall_test = 0;
     const bool f32 = h->prec.func == 1;
     const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);
     const bool timed = h->prof && flags == 0;
@@ -415,6 +417,14 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
             a.acc = h->acc[c];
             a.acc_hi = h->acc_hi[c];
             a.acc_lo = h->acc_lo[c];
+            if (kind == 1 && h->stall_ns > 0) {   // injected stall: this launch only
+                SweepArgs s = a;
+                s.stall_test = 1;
+                s.wait_ns = h->stall_ns;
+                h->stall_ns = 0;
+                CU(launch_sweep_f32_tma(h->prec, s, h->tma, h->nsm, h->stream));
+                continue;
+            }
             CU(!f32 ? launch_sweep(h->prec, a, h->stream)
                     : kind == 1 ? launch_sweep_f32_tma(h->prec, a, h->tma, h->nsm, h->stream)
                                 : launch_sweep_f32(h->prec, a, h->stream));
@@ -677,6 +687,17 @@ mpr_status mpr_get_info(mpr_handle h, mpr_info* info)
     info->sweep_kernel = h->prec.func == 0 ? -1
                          : !h->tma.ok ? 0
                          : h->sweep_force >= 0 ? h->sweep_force : h->sweep_kind;
+    return MPR_OK;
+}
+
+mpr_status mpr_inject_tma_stall(mpr_handle h, double timeout_s)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(h->prec.func == 1 && h->tma.ok))
+        return fail(MPR_ERR_INVALID_ARG, "the handle cannot run the TMA sweep kernel");
+    if (!(timeout_s > 0.0) || timeout_s > 10.0)
+        return fail(MPR_ERR_INVALID_ARG, "timeout %g s outside (0, 10]", timeout_s);
+    h->stall_ns = (long long)(timeout_s * 1e9);
     return MPR_OK;
 }
 

@@ -436,8 +436,10 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
 // hardware scheduler overlaps many blocks, hiding each tile's load latency); the finish kernel
 // shrinks the tile list and sets the loop condition. No grid barrier, no spin wait.
 
+// Compiled for 4 resident blocks per SM: the inlined plain tile (most passes) fits 64 registers;
+// the rarer energy and sampling variants are calls that may spill.
 template <typename S, int R, int TJ>
-__global__ void __launch_bounds__(256, tile_min_blocks<R>()) pass_kernel(const Args* __restrict__ A, int colour)
+__global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A, int colour)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const Ctl* ctl = A->ctl;

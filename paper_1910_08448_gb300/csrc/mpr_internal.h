@@ -61,6 +61,8 @@ struct SweepArgs {
     float qf, invTf;           // the same in FP32 for the FP32-function kernel (no FP64 on device)
     int* err;                  // device error word (MPR_ERR_DEVICE_TIMEOUT) or NULL
     long long wait_ns;         // limit of one device-side wait (TMA kernel)
+    int stall_test;            // test hook: block 0 of the TMA kernel issues no copy for its
+                               // first tile, so its wait runs out (see mpr_inject_tma_stall)
     PhiloxSched ph;            // Philox schedule of this pass (FP32-function single-problem kernels)
 };
 

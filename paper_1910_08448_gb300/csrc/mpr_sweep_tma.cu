@@ -1,0 +1,243 @@
+// mpr_sweep_tma.cu -- single-problem colour half-sweep for the FP32 function setting, sweep kernel
+// kind 1, plain passes: persistent blocks (3 per SM) walk 128 x 32 tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while a block updates tile t, the TMA unit copies the next tile's
+// three boxes (other colour with halo, own values, own frozen bits) into shared memory, completing
+// on one mbarrier, so the staging step is pure sin/cos work. Blocks that walk equal tiles stay in
+// step with each other (all convert, then all update), and the static tile split leaves part of
+// the last round idle; the handle keeps this kernel only where its own timing finds it faster
+// than kind 0 (mpr_sweep_f32.cu). Also the tensor maps (cuTensorMapEncodeTiled through the
+// runtime's driver entry point).
+#include "mpr.h"
+#include "mpr_tile_f32.cuh"
+#include "mpr_tma.cuh"
+
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
+
+namespace mpr {
+namespace {
+
+using namespace f32;
+
+constexpr int kTmaRows = 4;   // rows per thread of the TMA kernel's tiles (128 x 32)
+
+// Shared memory of the TMA kernel: the boxes the TMA unit writes (other colour rows y0-1 ..
+// y0+TY over columns j0-HL .. j0+TJ+HL-1; own rows; own mask words), the unit-vector tile, and
+// the barrier the copies complete on.
+template <typename S, int R> struct TmaSmem {
+    static constexpr int TY = kWarps * R;
+    static constexpr int HL = 16 / (int)sizeof(S);   // one 16-byte chunk left and right of the tile
+    static constexpr int BW = kTJ + 2 * HL;
+    static constexpr int MW = kTJ / 32;              // mask words per tile row
+    static constexpr uint32_t kBytes =
+        (uint32_t)(sizeof(S) * ((TY + 2) * BW + TY * kTJ) + 4 * TY * MW);
+    alignas(128) S other[TY + 2][BW];
+    alignas(128) S own[TY][kTJ];
+    alignas(128) uint32_t mbits[TY][MW];
+    alignas(16) TileSmem<R> t;
+    uint64_t bar;
+    int ok;
+};
+
+// Unit vectors of the other colour from the TMA box (see stage() for the global-memory form).
+template <typename S, int R, bool CHECK>
+__device__ __forceinline__ void convert(const SweepArgs& a, const TmaSmem<S, R>& sm, int y0,
+                                        int j0, int jb, int lj, int cb, float q, TileSmem<R>& t)
+{
+    using Sm = TmaSmem<S, R>;
+    constexpr int NR = (Sm::TY + 2 + kWarps - 1) / kWarps;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = warp + i * kWarps;
+        if (r >= Sm::TY + 2) break;
+        const int y = y0 - 1 + r;
+        Pack4<S> st;
+        load4(&sm.other[r][Sm::HL + lj], st);
+        const S halo = sm.other[r][lane == 0 ? Sm::HL - 1 : Sm::HL + kTJ];
+        unit_row<S, R, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st, halo, t);
+    }
+}
+
+// Plain passes only (no fused energy, no sampling): the handle runs those passes with
+// sweep_f32_kernel, whose per-tile energy partials it reduces.
+template <typename S, int R>
+__global__ void __launch_bounds__(256, 3)
+    sweep_f32_tma_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap m_other,
+                         const __grid_constant__ CUtensorMap m_own,
+                         const __grid_constant__ CUtensorMap m_mask)
+{
+    using Sm = TmaSmem<S, R>;
+    constexpr int TY = Sm::TY;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    Sm& sm = *reinterpret_cast<Sm*>(dsm);
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const bool leader = lane == 0 && warp == 0;
+    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    const int ntiles = ntx * ((a.Ly + TY - 1) / TY);
+    const int cb = a.colour ^ 1;
+    const int lj = 4 * lane;
+
+    // one thread issues the three copies of tile t; x offsets are multiples of 16 bytes
+    auto issue = [&](int t) {
+        const int j0 = (t % ntx) * kTJ, y0 = (t / ntx) * TY;
+        tma::arrive_expect_tx(&sm.bar, Sm::kBytes);
+        tma::load_2d(&sm.other[0][0], &m_other, &sm.bar, j0 - Sm::HL, y0 - 1);
+        tma::load_2d(&sm.own[0][0], &m_own, &sm.bar, j0, y0);
+        tma::load_2d(&sm.mbits[0][0], &m_mask, &sm.bar, j0 / 32, y0);
+    };
+    // the leader waits for tile `it`'s copies; a wait that runs out records the error, waits once
+    // more for the copy in flight, and stops the block at the next barrier
+    auto await = [&](uint32_t it) {
+        if (!tma::wait(&sm.bar, it & 1u, a.wait_ns)) {
+            if (a.err) atomicExch(a.err, (int)MPR_ERR_DEVICE_TIMEOUT);
+            tma::wait(&sm.bar, it & 1u, a.wait_ns);
+            sm.ok = 0;
+        }
+    };
+
+    int t = blockIdx.x;
+    if (leader) {
+        sm.ok = 1;
+        tma::mbar_init(&sm.bar, 1);
+        if (t < ntiles) {
+            if (!(a.stall_test && blockIdx.x == 0)) issue(t);
+            await(0);
+        }
+    }
+    __syncthreads();
+    for (uint32_t it = 0; t < ntiles; ++it) {
+        if (!sm.ok) return;   // uniform: read after a block barrier
+        const int j0 = (t % ntx) * kTJ, y0 = (t / ntx) * TY;
+        const int jb = j0 + lj;
+        Pack4<S> mine[R];
+        uint32_t bits[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {   // rows in the order row_of()
+            const int ly = warp * R + row_of<R>(i, a.colour);
+            load4(&sm.own[ly][lj], mine[i]);
+            bits[i] = (sm.mbits[ly][lane >> 3] >> (lj & 31)) & 0xFu;
+        }
+        const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
+        if (interior) convert<S, R, false>(a, sm, y0, j0, jb, lj, cb, a.qf, sm.t);
+        else convert<S, R, true>(a, sm, y0, j0, jb, lj, cb, a.qf, sm.t);
+        __syncthreads();   // unit vectors complete; the boxes are free for the next tile
+        const int tn = t + (int)gridDim.x;
+        if (leader && tn < ntiles) {
+            tma::fence_proxy_async();
+            issue(tn);
+        }
+
+        double e_d = 0.0;   // unused: no energy in plain passes
+        float e_f = 0.0f;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int ly = warp * R + row_of<R>(i, a.colour);
+            const int y = y0 + ly;
+            if (y < a.Ly)
+                update_row_i<S, R, false, 0, true>(i, a, y, ly, jb, lj, mine[i], bits[i], sm.t, e_d,
+                                                   e_f);
+        }
+        if (leader && tn < ntiles) await(it + 1);
+        __syncthreads();   // the unit vectors' readers are done; sm.ok is current
+        t = tn;
+    }
+}
+
+template <typename S>
+cudaError_t go_tma(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t st)
+{
+    if (a.flags & (kMeasure | kSample)) return cudaErrorInvalidValue;   // plain passes only
+    using Sm = TmaSmem<S, kTmaRows>;
+    auto kern = sweep_f32_tma_kernel<S, kTmaRows>;
+    // per instantiation, once: shared-memory opt-in and the resident blocks per SM
+    static const int bps = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Sm));
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, sizeof(Sm)) != cudaSuccess)
+            n = 1;
+        return n < 1 ? 1 : n;
+    }();
+    const int ntiles = ((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + Sm::TY - 1) / Sm::TY);
+    const int grid = ntiles < nsm * bps ? ntiles : nsm * bps;
+    const int c = a.colour;
+    kern<<<grid, dim3(32, kWarps), sizeof(Sm), st>>>(a, m.other[c ^ 1], m.own[c], m.mask[c]);
+    return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// 2-D map over a row-major [rows][cols] array with a row stride of cols elements.
+bool encode(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, void* base, int cols, int rows,
+            int box_x, int box_y)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * esize};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename S>
+bool make_maps_typed(const Layout& L, CUtensorMapDataType dt, void* const ang[2],
+                     uint32_t* const mb[2], TmaMaps* out)
+{
+    using Sm = TmaSmem<S, kTmaRows>;
+    // the boxes must fit inside the arrays: at least two tile columns and TY + 2 rows
+    if (L.pitch < Sm::BW || L.Ly < Sm::TY + 2) return false;
+    for (int c = 0; c < 2; ++c) {
+        if (!encode(&out->other[c], dt, sizeof(S), ang[c], L.pitch, L.Ly, Sm::BW, Sm::TY + 2) ||
+            !encode(&out->own[c], dt, sizeof(S), ang[c], L.pitch, L.Ly, kTJ, Sm::TY) ||
+            !encode(&out->mask[c], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, mb[c], L.mpitch, L.Ly,
+                    Sm::MW, Sm::TY))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+bool make_sweep_maps(const Layout& L, int store, void* const ang[2], uint32_t* const mb[2],
+                     TmaMaps* out)
+{
+    bool ok = false;
+    switch (store) {
+    case kF64: ok = make_maps_typed<double>(L, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, ang, mb, out); break;
+    case kF32: ok = make_maps_typed<float>(L, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ang, mb, out); break;
+    case kF16: ok = make_maps_typed<__half>(L, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, ang, mb, out); break;
+    case kBF16: ok = make_maps_typed<__nv_bfloat16>(L, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, ang, mb, out); break;
+    default: break;
+    }
+    out->ok = ok;
+    return ok;
+}
+
+cudaError_t launch_sweep_f32_tma(const Precision& p, const SweepArgs& a, const TmaMaps& m, int nsm,
+                                 cudaStream_t st)
+{
+    switch (p.store) {
+    case kF64: return go_tma<double>(a, m, nsm, st);
+    case kF32: return go_tma<float>(a, m, nsm, st);
+    case kF16: return go_tma<__half>(a, m, nsm, st);
+    case kBF16: return go_tma<__nv_bfloat16>(a, m, nsm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mpr

@@ -108,8 +108,9 @@ template <int R, int TJ = kTJ> struct TileSmem {
     float wsum_f[kWarps];
 };
 
-// Resident blocks per SM the tile kernels are compiled for: 4 (64 registers) for tiles of up to
-// 2 rows per warp, 3 (85 registers) for 4 rows per warp, whose row loop holds more values.
+// Resident blocks per SM for the tile variants with fused energy or sampling: 4 (64 registers)
+// for up to 2 rows per thread, 3 (85 registers) for 4 rows per thread, whose loop holds more
+// values. Plain passes compile for 4 in every case.
 template <int R> __host__ __device__ constexpr int tile_min_blocks() { return R >= 4 ? 3 : 4; }
 
 // 2^x on the MUFU (hand-written PTX: ex2.approx.ftz.f32)
@@ -287,8 +288,12 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             // h = 0 gives NaN in atan2_doubled, every comparison below is false and the angle
             // stays, as the move requires.
             float r = atan2_doubled(hyk, hxk) - q * f1;   // in [-pi - 2 pi q, pi]
-            r = r < 0.0f ? r + two_pi : r;
-            r = r < 0.0f ? r + two_pi : r;
+            // r < 0 ? r + 2 pi : r, twice, on the FMA pipe: the saturated product is 1 for every
+            // negative normal r and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the
+            // rounding of a plain add. (A nonzero r is never subnormal: its two terms are 0 or at
+            // least ~1e-8 in magnitude.)
+            r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
+            r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
             const float fn = r <= width ? r * inv_q : f1;
             if constexpr (sizeof(S) == 2) {
                 // 16-bit storage: the pair's two results rounded by one conversion and merged into

@@ -537,3 +537,87 @@ def test_sweep_kernel_choice(mpr, orc):
                 mpr.mpr_set_sweep_kernel(h, bad)
     finally:
         mpr.mpr_destroy(h)
+
+
+def test_tma_wait_timeout_is_reported(mpr, orc):
+    # The TMA kernel's mbarrier wait is bounded: with the copies of block 0's first tile left out
+    # (host-side injection), the wait runs out, the block records the error and returns, the
+    # launch ends normally and the next synchronising call reports MPR_ERR_DEVICE_TIMEOUT. The
+    # handle stays usable afterwards.
+    pr = mpr_inputs.make_problem(700, 300, 0.9, field_seed=47, mask_seed=48)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, "HDS", seed=2)
+        mpr.mpr_set_sweep_kernel(h, 1)
+        mpr.mpr_set_temperature(h, 0.3)
+        mpr.mpr_run(h, 2, 0)
+        mpr.mpr_inject_tma_stall(h, 0.05)
+        with pytest.raises(mpr.MPRError) as e:
+            mpr.mpr_run(h, 2, 0)
+        assert e.value.status == mpr.MPR_ERR_DEVICE_TIMEOUT
+        mpr.mpr_run(h, 2, 0)   # the error was reported once; the handle keeps working
+        st, sw = mpr.mpr_get_state(h)
+        assert sw == 6 and np.all(np.isfinite(st))
+    finally:
+        mpr.mpr_destroy(h)
+    q = mpr_inputs.make_problem(64, 64, 0.5, field_seed=49, mask_seed=50)
+    h = mpr.mpr_create(q.z, q.mask)
+    try:
+        with pytest.raises(mpr.MPRError):
+            mpr.mpr_inject_tma_stall(h, 0.05)   # no TMA kernel for a lattice this narrow
+    finally:
+        mpr.mpr_destroy(h)
+
+
+# --- the bench's workloads at full size, sampled --------------------------------------------
+
+@pytest.mark.parametrize("L,setup", [(4096, "HDS"), (16384, "SDS")])
+def test_full_size_sweep_sampled_sites(mpr, orc, L, setup):
+    # The workloads bench.py times (4096^2 and 16384^2, p = 0.9) through the C ABI in its launch
+    # configuration (the tile kernel, which the automatic choice keeps at these sizes): one sweep
+    # from an identical state; 2000 sampled sites of each colour are recomputed one by one by the
+    # oracle -- red sites from the initial state, black sites from the GPU's red neighbours -- and
+    # must agree within the FP32 tolerance outside near-threshold decisions. Frozen sites are
+    # compared in full, bit for bit.
+    import torch
+
+    dev = torch.device("cuda", 0)
+    pr = mpr_inputs.make_problem(L, L, 0.9, field_seed=1, mask_seed=101, periodic=L > 4096,
+                                 device=dev)
+    o = _oracle(orc, L, L, 7, setup)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    rng = np.random.default_rng(3)
+    state = np.where(pr.mask == 1, phi.reshape(L, L), rng.random((L, L)) * TWO_PI)
+    state = np.ascontiguousarray(_round_store(state, setup))
+    T, sweep = 0.07, 11
+    got, sw, info, _, _ = _gpu_sweeps(mpr, pr, setup, 7, state, sweep, T, 1)
+    # one sweep is too short for the automatic choice (-1: not chosen yet), which runs kind 0
+    assert sw == sweep + 1 and info["sweep_kernel"] in (-1, 0)
+    frozen = pr.mask == 1
+    assert np.array_equal(got[frozen].view(np.uint64), state[frozen].view(np.uint64))
+    col = _colour(L, L)
+    tol = 1e-4 + 2 * _ulp_store(setup)
+    work = state.copy()
+    mask8 = np.ascontiguousarray(pr.mask, dtype=np.uint8)   # passed to the oracle without a copy
+    for c in (0, 1):
+        ys, xs = np.nonzero((col == c) & ~frozen)
+        pick = rng.choice(ys.size, 2000, replace=False)
+        bad = excused = 0
+        for k in pick:
+            y, x = int(ys[k]), int(xs[k])
+            nbr = [(yy, xx) for yy, xx in ((y, x - 1), (y, x + 1), (y - 1, x), (y + 1, x))
+                   if 0 <= yy < L and 0 <= xx < L]
+            if c == 1:   # black: the GPU's red neighbours as inputs
+                for yy, xx in nbr:
+                    work[yy, xx] = got[yy, xx]
+            f, mm, om = o.update_site(work, mask8, x, y, T, sweep)
+            if c == 1:
+                for yy, xx in nbr:
+                    work[yy, xx] = state[yy, xx]
+            if mm < 1e-4 or om < 1e-4:
+                excused += 1
+                continue
+            if abs(got[y, x] - _round_store(np.array([f]), setup)[0]) > tol:
+                bad += 1
+        assert bad == 0, (c, bad)
+        assert excused < 40, (c, excused)
