@@ -131,6 +131,16 @@ mpr_status mpr_set_temperature(mpr_handle h, double T);   /* T > 0; bypasses the
  * and the accumulators carry over. STATE if no temperature is set. */
 mpr_status mpr_run(mpr_handle h, int equil, int samples);
 
+/* mpr_run with the length of the equilibration decided from the energy: sweeps in chunks of
+ * `chunk` (>= 2) with the bond energy e_b recorded after every sweep; after the second and every
+ * later chunk, equilibration ends when the chunk's mean e_b differs from the previous chunk's by
+ * at most 2 standard errors of the difference (sqrt((s_k^2 + s_{k-1}^2) / chunk), s^2 the chunks'
+ * sample variances), i.e. once the energy shows no drift a chunk can resolve, or after max_equil
+ * sweeps (whole chunks). Then `samples` accumulated sweeps as in mpr_run. The paper averages
+ * configurations "in equilibrium" without a rule for recognising it; this is one. *equil_done
+ * (may be NULL) receives the equilibration sweeps run. STATE if no temperature is set. */
+mpr_status mpr_run_auto(mpr_handle h, int chunk, int max_equil, int samples, int* equil_done);
+
 /* Prediction zhat = zmin + (zmax - zmin) * mean(phi) / (2*pi) at prediction sites, the measured
  * value elsewhere; out holds Lx*Ly doubles, row-major. STATE if no sample was taken. */
 mpr_status mpr_predict(mpr_handle h, double* out);

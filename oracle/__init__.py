@@ -99,6 +99,8 @@ def lib():
             L.mpro_run.restype = None
             L.mpro_tune.argtypes = [P(Cfg), vp, vp, d, P(u32), P(TuneCfg), P(d), vp, vp, P(i)]
             L.mpro_tune.restype = i
+            L.mpro_equilibrate.argtypes = [P(Cfg), vp, vp, d, P(u32), i, i, d]
+            L.mpro_equilibrate.restype = i
             L.mpro_predict.argtypes = [i, vp, i, vp, vp, d, d, vp]
             L.mpro_predict.restype = None
             _lib = L
@@ -244,6 +246,15 @@ class Oracle:
                              ctypes.byref(t), ctypes.byref(T), _ptr(tT), _ptr(te), ctypes.byref(n))
         trace = list(zip(tT[: n.value].tolist(), te[: n.value].tolist()))
         return st, T.value, phi, sw.value, trace
+
+    def equilibrate(self, phi, mask, T, sweep, chunk, max_sweeps, z=2.0):
+        """Energy-slope equilibration: returns (phi, sweeps run, next sweep)."""
+        phi = _f64(phi).copy()
+        m = _u8(mask)
+        sw = ctypes.c_uint32(sweep)
+        n = lib().mpro_equilibrate(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), T,
+                                   ctypes.byref(sw), chunk, max_sweeps, z)
+        return phi, n, sw.value
 
     def predict(self, acc, nsamples, z, mask, zmin, zmax) -> np.ndarray:
         acc = _f64(acc)

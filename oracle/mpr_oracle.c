@@ -312,6 +312,38 @@ void mpro_run(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, u
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Equilibration with an energy-slope stop. A reading, not the paper's: Sec. 2 averages          */
+/* configurations "in equilibrium" without saying how equilibrium is recognised. The energy of  */
+/* the chain drifts while it relaxes; equilibrium is declared when two consecutive chunks of    */
+/* sweeps have means that agree within z standard errors of their difference.                   */
+/* ------------------------------------------------------------------------------------------ */
+
+int mpro_equilibrate(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                     uint32_t* sweep, int chunk, int max_sweeps, double z)
+{
+    if (chunk < 2) return 0;
+    double* e = (double*)malloc(sizeof(double) * (size_t)chunk);
+    double prev_mean = 0.0, prev_var = 0.0;
+    int done = 0;
+    for (int k = 0; done + chunk <= max_sweeps; ++k) {
+        mpro_run(cfg, phi, mask, T, *sweep, chunk, NULL, e);
+        *sweep += (uint32_t)chunk;
+        done += chunk;
+        double mean = 0.0;
+        for (int i = 0; i < chunk; ++i) mean += e[i];
+        mean /= (double)chunk;
+        double var = 0.0;
+        for (int i = 0; i < chunk; ++i) var += (e[i] - mean) * (e[i] - mean);
+        var /= (double)(chunk - 1);
+        if (k > 0 && fabs(mean - prev_mean) <= z * sqrt((var + prev_var) / (double)chunk)) break;
+        prev_mean = mean;
+        prev_var = var;
+    }
+    free(e);
+    return done;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Temperature tuning (Sec. 2: the temperature is the only parameter and is inferred from the   */
 /* data). Reading: find T whose equilibrium bond energy of the conditional lattice equals the   */
 /* sample's, by bisection in log T; e_b(T) is non-decreasing because d<H>/dT = Var(H)/T^2.      */

@@ -90,6 +90,15 @@ int mpro_tune(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double e_s,
               const mpro_tune_cfg* tcfg, double* T_out, double* trace_T, double* trace_e,
               int* n_probes);
 
+/* Equilibration with an energy-slope stop (an option: the paper fixes no equilibration rule):
+ * sweeps in chunks of `chunk` (>= 2), e_b recorded after every sweep; after the second and every
+ * later chunk, stop when the chunk's mean differs from the previous chunk's by at most z standard
+ * errors of the difference, sqrt((s_k^2 + s_{k-1}^2) / chunk), s^2 the chunk's sample variance:
+ * no drift the chunk can resolve. At most max_sweeps sweeps (whole chunks). Returns the sweeps
+ * run; *sweep advances by them. */
+int mpro_equilibrate(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                     uint32_t* sweep, int chunk, int max_sweeps, double z);
+
 /* zhat = z on measured sites, zmin + (zmax - zmin) * (acc/nsamples) / (2*pi) elsewhere. */
 void mpro_predict(int N, const double* acc, int nsamples, const double* z, const uint8_t* mask,
                   double zmin, double zmax, double* zhat);

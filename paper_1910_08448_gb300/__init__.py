@@ -90,6 +90,7 @@ def load():
             "mpr_tune_temperature": ([H, P(d)], i),
             "mpr_set_temperature": ([H, d], i),
             "mpr_run": ([H, i, i], i),
+            "mpr_run_auto": ([H, i, i, i, P(i)], i),
             "mpr_predict": ([H, vp], i),
             "mpr_predict_dev": ([H, vp], i),
             "mpr_energy": ([H, P(d), P(d)], i),
@@ -128,7 +129,7 @@ def exported_symbols():
     """Names the binding expects the library to export (every function of include/mpr.h)."""
     return ["mpr_create", "mpr_create_dev", "mpr_destroy", "mpr_set_options", "mpr_get_options",
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
-            "mpr_run", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
+            "mpr_run", "mpr_run_auto", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
             "mpr_set_sweep_kernel", "mpr_inject_tma_stall",
             "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error",
@@ -238,6 +239,13 @@ def mpr_set_temperature(h, T: float):
 
 def mpr_run(h, equil: int, samples: int):
     _check(load().mpr_run(h, int(equil), int(samples)))
+
+
+def mpr_run_auto(h, chunk: int, max_equil: int, samples: int) -> int:
+    """Energy-slope equilibration then sampling; returns the equilibration sweeps run."""
+    n = ctypes.c_int()
+    _check(load().mpr_run_auto(h, int(chunk), int(max_equil), int(samples), ctypes.byref(n)))
+    return n.value
 
 
 def mpr_predict(h) -> np.ndarray:

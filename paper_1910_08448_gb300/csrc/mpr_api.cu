@@ -476,6 +476,15 @@ mpr_status mean_energy(mpr_ctx* h, int n, double* mean)
     return MPR_OK;
 }
 
+// e_b = -raw/N_b of the n measured sweeps of the last run, in sweep order.
+mpr_status energy_series(mpr_ctx* h, int n, double* e)
+{
+    CU(cudaMemcpyAsync(e, h->eseries, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CHECK(sync(h));
+    for (int k = 0; k < n; ++k) e[k] = -e[k] / (double)h->Nb;
+    return MPR_OK;
+}
+
 mpr_status probe(mpr_ctx* h, double T, double* e)
 {
     CHECK(sweeps(h, h->tune.n_eq, T, 0));
@@ -609,6 +618,46 @@ mpr_status mpr_run(mpr_handle h, int equil, int samples)
     if (equil < 0 || samples < 0) return fail(MPR_ERR_INVALID_ARG, "negative sweep count");
     if (!h->have_T) return fail(MPR_ERR_STATE, "no temperature: tune or set it first");
     CHECK(sweeps(h, equil, h->T, 0));
+    if (samples > 0) {
+        CHECK(sweeps(h, samples, h->T, kSample | kMeasure));
+        h->nsamples += samples;
+        CHECK(mean_energy(h, samples, &h->e_bond_mean));
+    } else {
+        CHECK(sync(h));
+    }
+    return MPR_OK;
+}
+
+// Energy-slope equilibration: chunks of measured sweeps until two consecutive chunk means agree
+// within kSlopeZ standard errors of their difference (the same rule as the oracle's
+// mpro_equilibrate), then the sampling sweeps of mpr_run.
+constexpr double kSlopeZ = 2.0;
+
+mpr_status mpr_run_auto(mpr_handle h, int chunk, int max_equil, int samples, int* equil_done)
+{
+    NvtxRange r("mpr_run_auto");
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (chunk < 2 || max_equil < 0 || samples < 0)
+        return fail(MPR_ERR_INVALID_ARG, "chunk %d must be >= 2, sweep counts >= 0", chunk);
+    if (!h->have_T) return fail(MPR_ERR_STATE, "no temperature: tune or set it first");
+    std::vector<double> e((size_t)chunk);
+    double prev_mean = 0.0, prev_var = 0.0;
+    int done = 0;
+    for (int k = 0; done + chunk <= max_equil; ++k) {
+        CHECK(sweeps(h, chunk, h->T, kMeasure));
+        CHECK(energy_series(h, chunk, e.data()));
+        done += chunk;
+        double mean = 0.0;
+        for (int i = 0; i < chunk; ++i) mean += e[(size_t)i];
+        mean /= (double)chunk;
+        double var = 0.0;
+        for (int i = 0; i < chunk; ++i) var += (e[(size_t)i] - mean) * (e[(size_t)i] - mean);
+        var /= (double)(chunk - 1);
+        if (k > 0 && fabs(mean - prev_mean) <= kSlopeZ * sqrt((var + prev_var) / (double)chunk)) break;
+        prev_mean = mean;
+        prev_var = var;
+    }
+    if (equil_done) *equil_done = done;
     if (samples > 0) {
         CHECK(sweeps(h, samples, h->T, kSample | kMeasure));
         h->nsamples += samples;

@@ -14,11 +14,11 @@ using namespace f32;
 
 constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 
-// Plain passes (no energy, no sampling: nearly all) compile for 4 resident blocks per SM (64
-// registers, no spills with 4-row tiles); the energy and sampling variants for tile_min_blocks.
+// Compiled for 4 resident blocks per SM (64 registers: no spills with 16-bit spins, a few bytes
+// with FP32 spins in the energy and sampling variants); 2 for FP64 spins, whose values take
+// twice the registers and would spill at 3 or 4.
 template <typename S, int R, bool MEASURE, int SAMPLE>
-__global__ void __launch_bounds__(256, (MEASURE || SAMPLE) ? tile_min_blocks<R>() : 4)
-    sweep_f32_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) sweep_f32_kernel(const SweepArgs a)
 {
     static_assert(R % 2 == 0, "the 64-column tail tile has R / 2 rows per thread");
     __shared__ __align__(16) TileSmem<R> sm;

@@ -108,10 +108,6 @@ template <int R, int TJ = kTJ> struct TileSmem {
     float wsum_f[kWarps];
 };
 
-// Resident blocks per SM for the tile variants with fused energy or sampling: 4 (64 registers)
-// for up to 2 rows per thread, 3 (85 registers) for 4 rows per thread, whose loop holds more
-// values. Plain passes compile for 4 in every case.
-template <int R> __host__ __device__ constexpr int tile_min_blocks() { return R >= 4 ? 3 : 4; }
 
 // 2^x on the MUFU (hand-written PTX: ex2.approx.ftz.f32)
 __device__ __forceinline__ float ex2_approx(float x)
@@ -257,6 +253,7 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
     }
     uint4 w;
     float fn_even = 0.0f;
+    float ev[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // MEASURE: u_b . h_b of the row's sites
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         // one Philox call per site pair, whether or not its sites update: no branch per site
@@ -329,9 +326,15 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             // every bond joins a red and a black site: sum over black sites of u_b . h_b
             float sn, cs;
             __sincosf(q * f, &sn, &cs);
-            const float e = cs * hxk + sn * hyk;
-            if (a.flags & kEnergyF32) e_f += e; else e_d += (double)e;
+            ev[k] = cs * hxk + sn * hyk;
         }
+    }
+    if (MEASURE) {
+        // the row's four FP32 terms pairwise in FP32 (two roundings of the size of the terms'
+        // own), then into the thread's FP64 (or FP32) sum: one FP64 add per row instead of four,
+        // on a part whose FP64 rate is a small fraction of its FP32 rate
+        const float er = (ev[0] + ev[1]) + (ev[2] + ev[3]);
+        if (a.flags & kEnergyF32) e_f += er; else e_d += (double)er;
     }
     store4(own + idx, pk);   // unchanged entries are written back with their own bits
 }

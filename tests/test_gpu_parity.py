@@ -621,3 +621,50 @@ def test_full_size_sweep_sampled_sites(mpr, orc, L, setup):
                 bad += 1
         assert bad == 0, (c, bad)
         assert excused < 40, (c, excused)
+
+
+# --- energy-slope equilibration ----------------------------------------------------------------
+
+def test_run_auto_matches_oracle_ddd(mpr, orc):
+    # mpr_run_auto against the oracle's mpro_equilibrate (same stopping rule): in FP64 the two
+    # chains and their energy series agree to rounding, so they stop after the same number of
+    # sweeps and end in the same state; then the samples as mpr_run.
+    pr = mpr_inputs.make_problem(64, 64, 0.33, field_seed=51, mask_seed=52)
+    o, state = _start_state(orc, pr, "DDD", 23)
+    T, chunk, ns = 0.05, 10, 5
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, "DDD", seed=23)
+        mpr.mpr_set_state(h, state, 0)
+        mpr.mpr_set_temperature(h, T)
+        n = mpr.mpr_run_auto(h, chunk, 5000, ns)
+        got, sw = mpr.mpr_get_state(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    p, n_o, sw_o = o.equilibrate(state, pr.mask, T, 0, chunk, 5000)
+    assert n == n_o and 2 * chunk <= n < 5000
+    p, _, e = o.run(p, pr.mask, T, sw_o, ns, energies=True)
+    assert sw == n + ns and info["n_samples"] == ns
+    assert np.mean(np.abs(got - p) < 1e-9) > 0.999
+
+
+@pytest.mark.parametrize("setup", ["HDS", "SDS"])
+def test_run_auto_reaches_the_long_run_energy(mpr, setup):
+    # FP32 functions: the stop comes after the relaxation, at the energy of a long plain run.
+    pr = mpr_inputs.make_problem(512, 512, 0.9, field_seed=53, mask_seed=54)
+    T = 0.06
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=5)
+        mpr.mpr_set_temperature(h, T)
+        n = mpr.mpr_run_auto(h, 20, 20000, 50)
+        e_stop = mpr.mpr_get_info(h)["e_bond_mean"]
+        mpr.mpr_run(h, 2000, 200)
+        e_long = mpr.mpr_get_info(h)["e_bond_mean"]
+        with pytest.raises(mpr.MPRError):
+            mpr.mpr_run_auto(h, 1, 100, 0)
+    finally:
+        mpr.mpr_destroy(h)
+    assert 40 <= n < 20000
+    assert abs(e_stop - e_long) < 2e-3, (n, e_stop, e_long)

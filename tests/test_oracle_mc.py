@@ -286,3 +286,48 @@ def test_tuning_edge_cases(orc):
     assert st == 0 and T == 1e-3 and len(tr) == 1 and sw == 30
     st, T, _, sw, tr = o.tune(phi, pr.mask, 0.5, 0, n_eq=20, n_meas=10)
     assert st == 4 and T == 10.0 and len(tr) == 2 and sw == 60
+
+
+# --- energy-slope equilibration ----------------------------------------------------------------
+
+def _relaxing_problem(orc):
+    import mpr_inputs
+
+    pr = mpr_inputs.make_problem(32, 32, 0.66, field_seed=3, mask_seed=4)
+    o = orc.Oracle(32, 32, seed=12)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    return pr, o, o.init(phi, pr.mask)   # a hot (uniform random) start
+
+
+def test_equilibrate_control_flow(orc):
+    pr, o, phi = _relaxing_problem(orc)
+    # an infinite tolerance accepts the first comparison: exactly two chunks
+    _, n, sw = o.equilibrate(phi, pr.mask, 0.1, 0, 25, 10000, z=math.inf)
+    assert n == 50 and sw == 50
+    # a zero tolerance never accepts (the chunk means of a continuous chain never tie): the cap
+    _, n, sw = o.equilibrate(phi, pr.mask, 0.1, 7, 25, 260, z=0.0)
+    assert n == 250 and sw == 257
+    # one chunk fits below the cap: nothing to compare, one chunk run; chunks below 2 run nothing
+    _, n, _ = o.equilibrate(phi, pr.mask, 0.1, 0, 25, 49)
+    assert n == 25
+    _, n, _ = o.equilibrate(phi, pr.mask, 0.1, 0, 1, 100)
+    assert n == 0
+    # the sweeps are the chain's ordinary sweeps: same state as a plain run of that length
+    p_eq, n, _ = o.equilibrate(phi, pr.mask, 0.1, 0, 25, 10000, z=math.inf)
+    p_run, _, _ = o.run(phi, pr.mask, 0.1, 0, n)
+    assert np.array_equal(p_eq, p_run)
+
+
+def test_equilibrate_stops_when_the_energy_has_relaxed(orc):
+    # From a hot start at low T the bond energy falls over the first tens of sweeps: the rule must
+    # not stop during the fall, and where it stops the energy must already sit at its long-run
+    # level.
+    pr, o, phi = _relaxing_problem(orc)
+    T, chunk = 0.05, 10
+    p_eq, n, sw = o.equilibrate(phi, pr.mask, T, 0, chunk, 20000)
+    assert 2 * chunk < n < 20000
+    _, _, e_before = o.run(phi, pr.mask, T, 0, n, energies=True)
+    _, _, e_after = o.run(p_eq, pr.mask, T, sw, 2000, energies=True)
+    drop = e_before[:chunk].mean() - e_after.mean()
+    assert drop > 0.05   # the relaxation was real: the first chunk lies far above the long run
+    assert abs(e_before[-chunk:].mean() - e_after.mean()) < 0.1 * drop
