@@ -35,6 +35,7 @@ class Cfg(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("problem", ctypes.c_uint32),
         ("ubits", ctypes.c_int),
+        ("width", ctypes.c_double),
     ]
 
 
@@ -85,12 +86,14 @@ def lib():
             L.mpro_init.restype = None
             L.mpro_overrelax.argtypes = [d, d, d, d, P(d)]
             L.mpro_overrelax.restype = d
-            L.mpro_update_site.argtypes = [P(Cfg), vp, vp, i, i, d, u32, P(d), P(d)]
+            L.mpro_update_site.argtypes = [P(Cfg), vp, vp, i, i, d, u32, P(d), P(d), P(i)]
             L.mpro_update_site.restype = d
             L.mpro_half_sweep.argtypes = [P(Cfg), vp, vp, d, u32, i, vp, vp]
-            L.mpro_half_sweep.restype = None
+            L.mpro_half_sweep.restype = ctypes.c_int64
             L.mpro_sweep.argtypes = [P(Cfg), vp, vp, d, u32, vp, vp]
-            L.mpro_sweep.restype = None
+            L.mpro_sweep.restype = ctypes.c_int64
+            L.mpro_run_adapt.argtypes = [P(Cfg), vp, vp, d, u32, i, d, vp]
+            L.mpro_run_adapt.restype = None
             L.mpro_energy_bond.argtypes = [P(Cfg), vp]
             L.mpro_energy_bond.restype = d
             L.mpro_energy_sample.argtypes = [P(Cfg), vp, vp, P(d), P(ctypes.c_int64)]
@@ -139,8 +142,8 @@ class Oracle:
     """One conditional MPR problem: an Lx x Ly grid with values z and a measured mask."""
 
     def __init__(self, Lx: int, Ly: int, seed: int = 0, q: float = 0.5, problem: int = 0,
-                 ubits: int = 32):
-        self.cfg = Cfg(Lx, Ly, q, seed, problem, ubits)
+                 ubits: int = 32, width: float = 0.0):
+        self.cfg = Cfg(Lx, Ly, q, seed, problem, ubits, width)
         self.Lx, self.Ly, self.q = Lx, Ly, q
 
     # --- random numbers ---------------------------------------------------------------------
@@ -177,8 +180,24 @@ class Oracle:
         m = _u8(mask)
         mm, om = ctypes.c_double(), ctypes.c_double()
         f = lib().mpro_update_site(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), x, y, T, sweep,
-                                   ctypes.byref(mm), ctypes.byref(om))
+                                   ctypes.byref(mm), ctypes.byref(om), None)
         return f, mm.value, om.value
+
+    def accepted(self, phi, mask, T, sweep) -> int:
+        """Accepted Metropolis proposals of one sweep from phi (the sweep itself is discarded)."""
+        phi = _f64(phi).copy()
+        m = _u8(mask)
+        return lib().mpro_sweep(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), T, sweep, None, None)
+
+    def run_adapt(self, phi, mask, T, sweep0, nsweeps, target):
+        """Adapted-width sweeps: returns (phi, widths used per sweep); the final width stays in
+        the oracle (self.cfg.width)."""
+        phi = _f64(phi).copy()
+        m = _u8(mask)
+        w = np.zeros(max(nsweeps, 1))
+        lib().mpro_run_adapt(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), T, sweep0, nsweeps,
+                             target, _ptr(w))
+        return phi, w[:nsweeps]
 
     def sweep(self, phi, mask, T, sweep, margins: bool = False):
         """Returns the new state (and the per-site Metropolis / over-relaxation margins)."""

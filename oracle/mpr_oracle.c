@@ -196,7 +196,8 @@ double mpro_overrelax(double q, double hx, double hy, double f, double* or_margi
 }
 
 double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* mask, int x, int y,
-                        double T, uint32_t sweep, double* met_margin, double* or_margin)
+                        double T, uint32_t sweep, double* met_margin, double* or_margin,
+                        int* accepted)
 {
     const double q = cfg->q;
     const int s = y * cfg->Lx + x;
@@ -205,26 +206,38 @@ double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* m
     local_field(cfg, phi, x, y, &hx, &hy);
 
     /* Metropolis. Reading: the proposal is an independent uniform angle on [0, 2*pi); the
-     * move is accepted when dE <= 0 or u < exp(-dE/T) (strict). */
+     * move is accepted when dE <= 0 or u < exp(-dE/T) (strict). Option (cfg->width > 0): a
+     * proposal f + w*(2u - 1) uniform on the segment of half-width w around f (symmetric, so the
+     * same acceptance rule holds), rejected when it leaves the state space [0, 2*pi). */
     uint32_t wp, wa;
     mpro_site_words(cfg, x, y, sweep, 0, &wp, &wa);
     double u_prop = mpro_uniform(cfg, wp);
     double u_acc = mpro_uniform(cfg, wa);
     double f = phi[s];
-    double f_prop = TWO_PI * u_prop;
+    const int bounded = cfg->width > 0.0;
+    double f_prop = bounded ? f + cfg->width * (2.0 * u_prop - 1.0) : TWO_PI * u_prop;
+    const int inside = !bounded || (f_prop >= 0.0 && f_prop < TWO_PI);
     double dE = site_energy(q, hx, hy, f_prop) - site_energy(q, hx, hy, f);
     double p_acc = (dE <= 0.0) ? 1.0 : exp(-dE / T);
-    int accept = (dE <= 0.0) || (u_acc < p_acc);
-    if (met_margin) *met_margin = fabs(u_acc - p_acc);
+    int accept = inside && ((dE <= 0.0) || (u_acc < p_acc));
+    if (met_margin) {
+        *met_margin = fabs(u_acc - p_acc);
+        if (bounded) {
+            const double edge = fmin(fabs(f_prop), fabs(TWO_PI - f_prop));
+            if (edge < *met_margin) *met_margin = edge;
+        }
+    }
+    if (accepted) *accepted = accept;
     double f1 = accept ? f_prop : f;
 
     return mpro_overrelax(q, hx, hy, f1, or_margin);
 }
 
-void mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
-                     uint32_t sweep, int colour, double* met_margin, double* or_margin)
+int64_t mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                        uint32_t sweep, int colour, double* met_margin, double* or_margin)
 {
     const int Lx = cfg->Lx, Ly = cfg->Ly;
+    int64_t n_acc = 0;
     /* A site reads only neighbours of the other colour, so the sites of one colour can be
      * overwritten in place. */
     for (int y = 0; y < Ly; ++y)
@@ -233,15 +246,18 @@ void mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, doub
             int s = y * Lx + x;
             if (mask[s]) continue;
             double mm, om;
-            double f = mpro_update_site(cfg, phi, mask, x, y, T, sweep, &mm, &om);
+            int acc;
+            double f = mpro_update_site(cfg, phi, mask, x, y, T, sweep, &mm, &om, &acc);
             phi[s] = f;
+            n_acc += acc;
             if (met_margin) met_margin[s] = mm;
             if (or_margin) or_margin[s] = om;
         }
+    return n_acc;
 }
 
-void mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,
-                double* met_margin, double* or_margin)
+int64_t mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,
+                   double* met_margin, double* or_margin)
 {
     const int N = cfg->Lx * cfg->Ly;
     if (met_margin)
@@ -249,8 +265,8 @@ void mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
     if (or_margin)
         for (int s = 0; s < N; ++s) or_margin[s] = INFINITY;
     /* red sites first, then black */
-    mpro_half_sweep(cfg, phi, mask, T, sweep, 0, met_margin, or_margin);
-    mpro_half_sweep(cfg, phi, mask, T, sweep, 1, met_margin, or_margin);
+    int64_t n = mpro_half_sweep(cfg, phi, mask, T, sweep, 0, met_margin, or_margin);
+    return n + mpro_half_sweep(cfg, phi, mask, T, sweep, 1, met_margin, or_margin);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -308,6 +324,30 @@ void mpro_run(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, u
         if (acc)
             for (int s = 0; s < N; ++s)
                 if (!mask[s]) acc[s] += phi[s];
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Bounded proposals with an adapted width. A reading, not the paper's (its proposal is not     */
+/* stated): after every sweep the width follows the sweep's acceptance fraction a of Metropolis */
+/* proposals toward a target, w <- w * exp(a - target), kept in [1e-3, 2*pi]. Adapting makes    */
+/* the chain time-inhomogeneous, so it belongs to equilibration; the width is then held fixed.  */
+/* ------------------------------------------------------------------------------------------ */
+
+void mpro_run_adapt(mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep0,
+                    int nsweeps, double target, double* widths)
+{
+    const int N = cfg->Lx * cfg->Ly;
+    int64_t n_pred = 0;
+    for (int s = 0; s < N; ++s) n_pred += mask[s] == 0;
+    for (int k = 0; k < nsweeps; ++k) {
+        if (widths) widths[k] = cfg->width;
+        const int64_t n_acc = mpro_sweep(cfg, phi, mask, T, sweep0 + (uint32_t)k, NULL, NULL);
+        const double a = n_pred > 0 ? (double)n_acc / (double)n_pred : target;
+        double w = cfg->width * exp(a - target);
+        if (w < 1e-3) w = 1e-3;
+        if (w > TWO_PI) w = TWO_PI;
+        cfg->width = w;
     }
 }
 

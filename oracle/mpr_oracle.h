@@ -29,6 +29,8 @@ typedef struct {
     uint64_t seed;       /* Philox key (low word, high word) */
     uint32_t problem;    /* problem id, part of the Philox counter */
     int ubits;           /* uniform resolution: 32 -> u = w*2^-32, 23 -> u = (w>>9)*2^-23 */
+    double width;        /* Metropolis proposal: 0 -> uniform angle on [0, 2*pi); w > 0 ->
+                            phi + w*(2u - 1), rejected outside [0, 2*pi) */
 } mpro_cfg;
 
 typedef struct {
@@ -59,18 +61,28 @@ void mpro_init(const mpro_cfg* cfg, const uint8_t* mask, double* phi);
 double mpro_overrelax(double q, double hx, double hy, double f, double* or_margin);
 
 /* One hybrid move (Metropolis, then over-relaxation) of prediction site (x, y) against the
- * current neighbour angles; returns the new angle. met_margin = |u_acc - min(1, exp(-dE/T))|,
- * or_margin = distance of the reflected angle to the ends of its admissible interval. */
+ * current neighbour angles; returns the new angle. met_margin = |u_acc - min(1, exp(-dE/T))|
+ * (bounded proposals: also the distance of the proposal to the ends of [0, 2*pi)), or_margin =
+ * distance of the reflected angle to the ends of its admissible interval; accepted (may be NULL)
+ * = 1 when the Metropolis proposal was accepted. */
 double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* mask, int x, int y,
-                        double T, uint32_t sweep, double* met_margin, double* or_margin);
+                        double T, uint32_t sweep, double* met_margin, double* or_margin,
+                        int* accepted);
 /* The prediction sites of one colour (0 red, 1 black); margins as for mpro_sweep, written only at
- * the sites it updates. */
-void mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
-                     uint32_t sweep, int colour, double* met_margin, double* or_margin);
+ * the sites it updates. Returns the accepted Metropolis proposals. */
+int64_t mpro_half_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T,
+                        uint32_t sweep, int colour, double* met_margin, double* or_margin);
 /* One hybrid sweep: all red prediction sites, then all black ones. The margin arrays (N, may be
- * NULL) receive each updated site's margins; other entries are set to +inf. */
-void mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,
-                double* met_margin, double* or_margin);
+ * NULL) receive each updated site's margins; other entries are set to +inf. Returns the accepted
+ * Metropolis proposals. */
+int64_t mpro_sweep(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep,
+                   double* met_margin, double* or_margin);
+/* Bounded proposals with an adapted width (an option, see mpr_oracle.c): nsweeps sweeps; after
+ * each, width <- clamp(width * exp(a - target), width_min, 2*pi) with a the sweep's accepted
+ * fraction of Metropolis proposals. cfg->width is the starting width and receives the final one;
+ * widths (nsweeps, may be NULL) records the width each sweep used. */
+void mpro_run_adapt(mpro_cfg* cfg, double* phi, const uint8_t* mask, double T, uint32_t sweep0,
+                    int nsweeps, double target, double* widths);
 
 /* e_b = -(1/N_b) sum over nearest-neighbour bonds of cos[q(phi_i - phi_j)]. */
 double mpro_energy_bond(const mpro_cfg* cfg, const double* phi);

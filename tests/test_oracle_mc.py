@@ -111,7 +111,7 @@ def _exact_moments(Lx, Ly, frozen, T, n=48):
     return e, means
 
 
-def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000):
+def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000, width=0.0):
     mask = np.zeros((Ly, Lx), np.uint8)
     phi = np.zeros((Ly, Lx))
     for s, a in frozen.items():
@@ -119,7 +119,7 @@ def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000):
         phi.flat[s] = a
     es, ms = [], []
     for c in range(chains):
-        o = orc.Oracle(Lx, Ly, seed=1000 + c)
+        o = orc.Oracle(Lx, Ly, seed=1000 + c, width=width)
         p = o.init(phi, mask)
         p, _, _ = o.run(p, mask, T, 0, equil)
         p, acc, e = o.run(p, mask, T, equil, nsweeps, acc=np.zeros_like(p), energies=True)
@@ -331,3 +331,97 @@ def test_equilibrate_stops_when_the_energy_has_relaxed(orc):
     drop = e_before[:chunk].mean() - e_after.mean()
     assert drop > 0.05   # the relaxation was real: the first chunk lies far above the long run
     assert abs(e_before[-chunk:].mean() - e_after.mean()) < 0.1 * drop
+
+
+# --- bounded Metropolis proposals with an adapted width ----------------------------------------
+
+@pytest.mark.parametrize("case", [0, 2, 3])
+@pytest.mark.parametrize("width", [0.4, 2.5])
+def test_bounded_proposal_samples_the_same_gibbs_measure(orc, case, width):
+    # A symmetric proposal on the segment of half-width w around the angle, rejected outside
+    # [0, 2 pi): the chain must sample the same conditional Gibbs measure as with the uniform one.
+    Lx, Ly, frozen, T = CASES[case]
+    e_ex, m_ex = _exact_moments(Lx, Ly, frozen, T)
+    e_mc, e_se, m_mc, m_se = _mc_moments(orc, Lx, Ly, frozen, T, width=width)
+    assert abs(e_mc - e_ex) < 4.5 * e_se + 1e-4, (e_mc, e_ex, e_se)
+    for s, v in m_ex.items():
+        y, x = divmod(s, Lx)
+        assert abs(m_mc[y, x] - v) < 4.5 * m_se[y, x] + 1e-3, (s, m_mc[y, x], v, m_se[y, x])
+
+
+def test_width_adaptation_reaches_target_acceptance(orc):
+    import mpr_inputs
+
+    pr = mpr_inputs.make_problem(48, 48, 0.66, field_seed=7, mask_seed=8)
+    T, target = 0.05, 0.5
+    o = orc.Oracle(48, 48, seed=4, width=2.0 * math.pi)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    n_pred = int((pr.mask == 0).sum())
+    # the uniform-like start accepts few proposals at this temperature
+    a0 = o.accepted(phi, pr.mask, T, 0) / n_pred
+    phi, widths = o.run_adapt(phi, pr.mask, T, 0, 400, target)
+    assert widths[0] == 2.0 * math.pi and widths[-1] < 0.5 * widths[0]
+    # widths follow the rule: w_{k+1} = w_k exp(a_k - target), within [1e-3, 2 pi]
+    assert np.all((widths > 1e-3 - 1e-15) & (widths <= 2.0 * math.pi))
+    # with the adapted width held fixed, the acceptance sits near the target
+    acc = [o.accepted(phi, pr.mask, T, 400 + k) / n_pred for k in range(20)]
+    assert a0 < 0.3 and abs(np.mean(acc) - target) < 0.1, (a0, np.mean(acc), o.cfg.width)
+
+
+def _gauss_seidel_ground_state(phi, mask, q=0.5, sweeps=20000, tol=1e-13):
+    # Independent FP64 minimiser of Eq. 2: each free angle in turn moves to the exact minimiser of
+    # its site energy -|h| cos(q phi - theta) over phi in [0, 2 pi] (q phi = theta when that lies
+    # in [0, 2 pi q], else the nearer end of the segment in angle), until nothing moves.
+    phi = phi.copy()
+    Ly, Lx = phi.shape
+    free = [(y, x) for y in range(Ly) for x in range(Lx) if mask[y, x] == 0]
+    for _ in range(sweeps):
+        moved = 0.0
+        for y, x in free:
+            hx = hy = 0.0
+            for yy, xx in ((y, x - 1), (y, x + 1), (y - 1, x), (y + 1, x)):
+                if 0 <= yy < Ly and 0 <= xx < Lx:
+                    hx += math.cos(q * phi[yy, xx])
+                    hy += math.sin(q * phi[yy, xx])
+            th = math.atan2(hy, hx) % (2.0 * math.pi)
+            if th <= 2.0 * math.pi * q:
+                new = th / q
+            else:
+                # distance in angle from theta to the two ends 0 and 2 pi q of the segment
+                d0 = min(th, 2.0 * math.pi - th)
+                d1 = abs(th - 2.0 * math.pi * q)
+                new = 0.0 if d0 < d1 else 2.0 * math.pi
+            moved = max(moved, abs(new - phi[y, x]))
+            phi[y, x] = new
+        if moved < tol:
+            break
+    return phi
+
+
+def _energy_eq2(phi, q=0.5):
+    return -(np.cos(q * (phi[:, 1:] - phi[:, :-1])).sum() + np.cos(q * (phi[1:, :] - phi[:-1, :])).sum())
+
+
+def test_low_temperature_2d_matches_gauss_seidel_minimiser(orc):
+    # T -> 0 on a 2-D conditional lattice: the annealed chain's mean configuration is the ground
+    # state an independent coordinate-wise minimiser finds (Sec. 2, Eq. 2 at vanishing T)
+    import mpr_inputs
+
+    pr = mpr_inputs.make_problem(12, 12, 0.5, field_seed=31, mask_seed=32)
+    o = orc.Oracle(12, 12, seed=33)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    phi = o.init(phi, pr.mask)
+    T = 1e-4
+    phi, sweep = _anneal(orc, o, phi, pr.mask, T, stages=30, per=300)
+    n = 2000
+    _, acc, _ = o.run(phi, pr.mask, T, sweep, n, acc=np.zeros_like(phi))
+    mean = np.where(pr.mask == 1, phi, acc / n)
+    start = np.where(pr.mask == 1, phi, math.pi)
+    gs = _gauss_seidel_ground_state(start, pr.mask)
+    gs_from_mean = _gauss_seidel_ground_state(mean, pr.mask)
+    # the chain's mean sits at a minimum (the minimiser barely moves it) ...
+    assert np.max(np.abs(gs_from_mean - mean)) < 0.02
+    # ... and no higher than the one the minimiser reaches from its own start
+    assert _energy_eq2(gs_from_mean) <= _energy_eq2(gs) + 1e-9
+    assert np.max(np.abs(gs_from_mean - gs)) < 1e-6 or _energy_eq2(gs_from_mean) < _energy_eq2(gs) - 1e-9
