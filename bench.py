@@ -170,7 +170,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 
 KERNEL_SOURCES = {
-    "mpr::sweep_f32_kernel": ("mpr_tile_f32.cuh", "mpr_sweep_f32.cu", "mpr_device.cuh"),
+    "mpr::sweep_f32_kernel": ("mpr_tile_f32.cuh", "mpr_sweep_f32.cuh", "mpr_device.cuh"),
     "mpr::sweep_f32_tma_kernel": ("mpr_tile_f32.cuh", "mpr_sweep_tma.cu", "mpr_tma.cuh",
                                   "mpr_device.cuh"),
     "mpr::sweep_kernel": ("mpr_sweep.cu", "mpr_device.cuh"),

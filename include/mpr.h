@@ -156,7 +156,7 @@ mpr_status mpr_get_info(mpr_handle h, mpr_info* info);
 mpr_status mpr_set_profiling(mpr_handle h, int on);
 
 /* Sweep kernel of the FP32-function setups; both compute identical states, bit for bit.
- * kind 0: one tile (128 half-lattice columns x 16 rows) per block, staged with ordinary loads.
+ * kind 0: one tile (128 half-lattice columns x 32 rows) per block, staged with ordinary loads.
  * kind 1: persistent blocks over 128 x 32 tiles; the TMA unit copies the next tile's boxes into
  *         shared memory (cp.async.bulk.tensor, mbarrier with a bounded wait) while the block
  *         updates the current one. Needs a lattice at least two tiles wide (Lx > 256) and 34 rows.
@@ -167,6 +167,20 @@ mpr_status mpr_set_profiling(mpr_handle h, int on);
  * INVALID_ARG if kind is not -1, 0 or 1, or kind 1 is unavailable for the handle. A forced kind
  * stays across mpr_set_options while it remains available; an automatic choice is redone. */
 mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind);
+
+/* Metropolis proposal of the handle's sweeps. The paper's hybrid step (Sec. 2) is read as an
+ * independent uniform proposal on [0, 2 pi), the default (width = 0). width in (0, 2 pi] selects
+ * the bounded proposal phi' = phi + width (2u - 1), u uniform on [0, 1) from the same Philox
+ * word, rejected when phi' leaves [0, 2 pi); the acceptance rule is unchanged (the proposal is
+ * symmetric). target in (0, 1) adapts the width after every sweep that does not sample:
+ * w <- w exp(a - target), a = the sweep's accepted proposals / n_pred, w kept in [1e-3, 2 pi]; the
+ * width then stays fixed while sampling (target = 0: fixed width). The width lives on the
+ * device; both FP32 and FP64 function setups support it, the FP32 ones through sweep kernel
+ * kind 0 only (mpr_get_info reports kind 0 while it is on). Synchronises the handle's stream.
+ * INVALID_ARG for width outside [0, 2 pi] or target outside [0, 1). */
+mpr_status mpr_set_proposal(mpr_handle h, double width, double target);
+/* Current half-width of the bounded proposal (0 when proposals are uniform); synchronises. */
+mpr_status mpr_get_proposal(mpr_handle h, double* width);
 
 /* Test hook for the bounded wait of the TMA kernel: in the next pass that runs with kind 1, block
  * 0 issues no copy for its first tile, so its mbarrier wait runs out after timeout_s (0 < timeout_s

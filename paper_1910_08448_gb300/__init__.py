@@ -98,6 +98,8 @@ def load():
             "mpr_set_profiling": ([H, i], i),
             "mpr_set_sweep_kernel": ([H, i], i),
             "mpr_inject_tma_stall": ([H, d], i),
+            "mpr_set_proposal": ([H, d, d], i),
+            "mpr_get_proposal": ([H, P(d)], i),
             "mpr_get_state": ([H, vp, P(u32)], i),
             "mpr_set_state": ([H, vp, u32], i),
             "mpr_philox4x32_10_dev": ([vp, vp, i, u64, vp], i),
@@ -131,7 +133,7 @@ def exported_symbols():
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_run", "mpr_run_auto", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
-            "mpr_set_sweep_kernel", "mpr_inject_tma_stall",
+            "mpr_set_sweep_kernel", "mpr_inject_tma_stall", "mpr_set_proposal", "mpr_get_proposal",
             "mpr_bond_energy_noalloc", "mpr_status_string", "mpr_last_error",
             "mpr_batch_create", "mpr_batch_destroy", "mpr_batch_set_stream",
             "mpr_batch_set_tuning", "mpr_batch_set_launch", "mpr_batch_autotune",
@@ -280,6 +282,19 @@ def mpr_set_profiling(h, on: bool = True):
 def mpr_set_sweep_kernel(h, kind: int):
     """FP32-function sweep kernel: -1 automatic (default), 0 one tile per block, 1 TMA-fed."""
     _check(load().mpr_set_sweep_kernel(h, int(kind)))
+
+
+def mpr_set_proposal(h, width: float = 0.0, target: float = 0.0):
+    """Metropolis proposal: width 0 uniform (default); else phi + width (2u - 1), rejected outside
+    [0, 2 pi), adapted toward acceptance fraction ``target`` while not sampling (0: fixed)."""
+    _check(load().mpr_set_proposal(h, float(width), float(target)))
+
+
+def mpr_get_proposal(h) -> float:
+    """Current half-width of the bounded proposal (0.0 when proposals are uniform)."""
+    w = ctypes.c_double()
+    _check(load().mpr_get_proposal(h, ctypes.byref(w)))
+    return w.value
 
 
 def mpr_inject_tma_stall(h, timeout_s: float = 0.05):
@@ -433,7 +448,9 @@ def mpr_last_error() -> str:
 
 
 class GapFiller:
-    """Owns one handle: ``GapFiller(z, mask, setup='SDS').fill(equil, samples)``."""
+    """Owns one handle: ``GapFiller(z, mask, setup='SDS').fill(equil, samples)``, or step by step
+    ``p.tune(); p.run(equil, samples); p.predict()``. Values and mask are numpy arrays (host) or
+    CUDA tensors (device, read on ``stream``)."""
 
     def __init__(self, values, mask, setup: str = "SDS", seed: int = 0, q: float = 0.5,
                  acc: str = "f64", stream=None):
@@ -448,11 +465,29 @@ class GapFiller:
 
     def fill(self, equil: int, samples: int, T=None):
         if T is None:
-            self.T, self.tune_status = mpr_tune_temperature(self.h)
+            self.tune()
         else:
-            mpr_set_temperature(self.h, T)
-            self.T, self.tune_status = T, MPR_OK
+            self.set_temperature(T)
+        self.run(equil, samples)
+        return self.predict()
+
+    def tune(self):
+        """Temperature tuning (returns T; the status is kept in ``tune_status``)."""
+        self.T, self.tune_status = mpr_tune_temperature(self.h)
+        return self.T
+
+    def set_temperature(self, T: float):
+        mpr_set_temperature(self.h, T)
+        self.T, self.tune_status = T, MPR_OK
+
+    def run(self, equil: int, samples: int):
         mpr_run(self.h, equil, samples)
+
+    def predict(self, out=None):
+        """Prediction as a numpy array, or written into the CUDA tensor ``out``."""
+        if out is not None:
+            mpr_predict_dev(self.h, out)
+            return out
         return mpr_predict(self.h)
 
     def info(self):
@@ -472,3 +507,6 @@ class GapFiller:
             self.close()
         except Exception:
             pass
+
+
+Problem = GapFiller

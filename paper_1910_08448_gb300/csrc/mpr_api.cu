@@ -126,6 +126,10 @@ struct mpr_ctx {
     int sweep_force = -1;                // mpr_set_sweep_kernel: -1 automatic, 0, 1
     long long stall_ns = 0;              // mpr_inject_tma_stall: wait limit of the next TMA pass
     int sweep_kind = -1;                 // automatic choice (-1 until made)
+    // bounded Metropolis proposals (mpr_set_proposal): the half-width lives on the device in
+    // scal[14], the acceptance counter of the adaptation in scal[13]
+    bool prop_on = false;
+    double prop_target = 0.0;            // target acceptance fraction; 0: fixed width
     cudaEvent_t cal[4] = {nullptr, nullptr, nullptr, nullptr};   // timing of the choice
 };
 
@@ -134,6 +138,11 @@ constexpr int kCalSweeps = 5;            // timed sweeps per kernel in the autom
 // Device error word of the handle: the last of the 16 device scalars (zeroed at creation).
 inline int* dev_err(mpr_ctx* h) { return reinterpret_cast<int*>(h->scal + 15); }
 inline int* host_err(mpr_ctx* h) { return reinterpret_cast<int*>(h->host + 15); }
+// Accepted bounded proposals of the current sweep (device scalar 13, as an integer).
+inline unsigned long long* prop_count(mpr_ctx* h)
+{
+    return reinterpret_cast<unsigned long long*>(h->scal + 13);
+}
 
 namespace {
 
@@ -398,6 +407,10 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.err = dev_err(h);
     a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds
     a.stall_test = 0;
+    // bounded proposals; the width adapts after every sweep that does not sample
+    const bool adapt = h->prop_on && h->prop_target > 0.0 && !(flags & kSample);
+    a.width = h->prop_on ? h->scal + 14 : nullptr;
+    a.accepted = adapt ? prop_count(h) : nullptr;
     const bool f32 = h->prec.func == 1;
     const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);
     const bool timed = h->prof && flags == 0;
@@ -430,12 +443,14 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
                                 : launch_sweep_f32(h->prec, a, h->stream));
         }
         if (flags & kMeasure) CU(launch_reduce(h->prec, h->part, nblk, h->eseries + k, h->stream));
-        h->launches += (flags & kMeasure) ? 3 : 2;
+        if (adapt) CU(launch_adapt_width(h->scal + 14, prop_count(h), h->Np, h->prop_target, h->stream));
+        h->launches += ((flags & kMeasure) ? 3 : 2) + (adapt ? 1 : 0);
         ++h->sweep;
         h->site_updates += (uint64_t)h->Np;
         return MPR_OK;
     };
-    const bool tma_ok = f32 && h->tma.ok && !(flags & kMeasure);
+    // the TMA kernel draws uniform proposals only
+    const bool tma_ok = f32 && h->tma.ok && !(flags & kMeasure) && !h->prop_on;
     int k = 0;
     if (tma_ok && h->sweep_force < 0 && h->sweep_kind < 0 && flags == 0 && n >= 2 * (1 + kCalSweeps)) {
         // automatic choice: one warm-up and kCalSweeps timed sweeps of each kernel, as ordinary
@@ -734,7 +749,7 @@ mpr_status mpr_get_info(mpr_handle h, mpr_info* info)
     info->prof_sweep_ms = h->prof_ms;
     info->prof_sweep_launches = h->prof_launches;
     info->sweep_kernel = h->prec.func == 0 ? -1
-                         : !h->tma.ok ? 0
+                         : (!h->tma.ok || h->prop_on) ? 0
                          : h->sweep_force >= 0 ? h->sweep_force : h->sweep_kind;
     return MPR_OK;
 }
@@ -747,6 +762,36 @@ mpr_status mpr_inject_tma_stall(mpr_handle h, double timeout_s)
     if (!(timeout_s > 0.0) || timeout_s > 10.0)
         return fail(MPR_ERR_INVALID_ARG, "timeout %g s outside (0, 10]", timeout_s);
     h->stall_ns = (long long)(timeout_s * 1e9);
+    return MPR_OK;
+}
+
+mpr_status mpr_set_proposal(mpr_handle h, double width, double target)
+{
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(width >= 0.0) || width > 6.283185307179586)
+        return fail(MPR_ERR_INVALID_ARG, "proposal half-width %g outside [0, 2 pi]", width);
+    if (!(target >= 0.0) || target >= 1.0)
+        return fail(MPR_ERR_INVALID_ARG, "target acceptance %g outside [0, 1)", target);
+    CHECK(sync(h));
+    h->prop_on = width > 0.0;
+    h->prop_target = h->prop_on ? target : 0.0;
+    h->host[14] = width;
+    CU(cudaMemcpyAsync(h->scal + 14, h->host + 14, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(prop_count(h), 0, sizeof(unsigned long long), h->stream));
+    return sync(h);
+}
+
+mpr_status mpr_get_proposal(mpr_handle h, double* width)
+{
+    if (!h || !width) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (!h->prop_on) {
+        CHECK(sync(h));
+        *width = 0.0;
+        return MPR_OK;
+    }
+    CU(cudaMemcpyAsync(h->host + 14, h->scal + 14, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CHECK(sync(h));
+    *width = h->host[14];
     return MPR_OK;
 }
 

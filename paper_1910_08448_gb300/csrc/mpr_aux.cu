@@ -303,6 +303,17 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, uint32_t* __rest
     reinterpret_cast<uint4*>(out)[i] = philox4x32_10(c, k0, k1);
 }
 
+// Width of the bounded Metropolis proposals after one sweep: w <- w exp(a - target), with a the
+// sweep's acceptance fraction over the n_pred prediction sites, kept in [1e-3, 2 pi]; the
+// counter restarts at 0 for the next sweep.
+__global__ void adapt_width_kernel(double* __restrict__ width, unsigned long long* __restrict__ count,
+                                   long long n_pred, double target)
+{
+    const double acc = n_pred > 0 ? (double)*count / (double)n_pred : target;
+    *width = fmin(fmax(*width * exp(acc - target), 1e-3), 6.283185307179586);
+    *count = 0ull;
+}
+
 inline int grid_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
 template <typename Fn>
@@ -422,6 +433,13 @@ cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* 
                                                              static_cast<S*>(ang1));
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_adapt_width(double* width, unsigned long long* count, long long n_pred,
+                               double target, cudaStream_t st)
+{
+    adapt_width_kernel<<<1, 1, 0, st>>>(width, count, n_pred, target);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed, cudaStream_t st)

@@ -64,6 +64,10 @@ struct SweepArgs {
     int stall_test;            // test hook: block 0 of the TMA kernel issues no copy for its
                                // first tile, so its wait runs out (see mpr_inject_tma_stall)
     PhiloxSched ph;            // Philox schedule of this pass (FP32-function single-problem kernels)
+    const double* width;       // bounded Metropolis proposals: device address of the half-width
+                               // (NULL: uniform proposals)
+    unsigned long long* accepted;  // bounded proposals: accepted proposals of the pass's
+                                   // prediction sites are added here (NULL: not counted)
 };
 
 // TMA descriptors of one problem's half-lattices for the TMA-fed FP32 sweep kernel: per colour c
@@ -81,6 +85,7 @@ int sweep_blocks(const Layout& L, const Precision& p);
 cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st);
 int sweep_f32_blocks(const Layout& L);
 cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_sweep_f32_prop(const Precision& p, const SweepArgs& a, cudaStream_t st);
 // TMA kernel: maps for the layout and storage (false when the lattice is too small for its boxes,
 // or the driver has no tensor maps; the one-tile-per-block kernel then runs); the launch of a
 // plain pass (no kMeasure, no kSample) on nsm SMs.
@@ -116,6 +121,9 @@ cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* 
                              const unsigned char* mask, void* ang0, void* ang1, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed,
                           cudaStream_t st);
+// One step of the proposal-width adaptation (bounded proposals): reads and clears *count.
+cudaError_t launch_adapt_width(double* width, unsigned long long* count, long long n_pred,
+                               double target, cudaStream_t st);
 
 // Sets the message returned by mpr_last_error() on the calling thread.
 void set_last_error(const char* msg);

@@ -70,6 +70,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
     const F T = (F)a.T, invT = (F)a.invT;
     const F two_pi = M::two_pi();
     const F width = two_pi * q;
+    const bool bounded = a.width != nullptr;
+    const F pw = bounded ? (F)*a.width : (F)0;   // bounded proposals: half-width
+    int n_acc = 0;
     E eacc = (E)0;
 
     for (int rr = 0; rr < R; ++rr) {
@@ -104,14 +107,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             if (upd[t]) {
                 const uint32_t wp = t ? w.z : w.x, wa = t ? w.w : w.y;
                 const F u_prop = M::uniform(wp), u_acc = M::uniform(wa);
-                // Metropolis: uniform proposal, accept if dE <= 0 or u < exp(-dE/T)
-                const F fp = two_pi * u_prop;
+                // Metropolis: uniform proposal (or bounded: f + pw (2u - 1), rejected outside
+                // [0, 2 pi)), accept if dE <= 0 or u < exp(-dE/T)
+                const F fp = bounded ? f + pw * ((F)2 * u_prop - (F)1) : two_pi * u_prop;
+                const bool inside = !bounded || (fp >= (F)0 && fp < two_pi);
                 F s0, c0, sp, cp;
                 M::sincos_(q * f, &s0, &c0);
                 M::sincos_(q * fp, &sp, &cp);
                 const F dE = (-(hx * cp + hy * sp)) - (-(hx * c0 + hy * s0));
                 bool accept = dE <= (F)0;
                 if (!accept) accept = u_acc < M::exp_neg_over(dE, T, invT);
+                accept = accept && inside;
+                n_acc += accept ? 1 : 0;
                 const F f1 = accept ? fp : f;
                 // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q]
                 F fn = f1;
@@ -146,6 +153,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
         }
     }
 
+    if (a.accepted) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, off);
+        if (threadIdx.x == 0 && n_acc) atomicAdd(a.accepted, (unsigned long long)n_acc);
+    }
     if (measure) {
 #pragma unroll
         for (int off = 16; off; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);

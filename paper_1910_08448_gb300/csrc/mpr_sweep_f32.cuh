@@ -1,0 +1,94 @@
+// mpr_sweep_f32.cuh -- single-problem colour half-sweep for the FP32 function setting, sweep
+// kernel kind 0: one launch per colour pass, one 128 x 32 tile of mpr_tile_f32.cuh per block, 4
+// blocks per SM (plain passes), staging with ordinary loads. The hardware block scheduler overlaps
+// one block's loads with other blocks' work, and blocks that start and end at different times keep
+// the SM's pipes evenly loaded. The alternative kernel kind 1 (TMA-fed, persistent) is in
+// mpr_sweep_tma.cu; both apply the same per-site arithmetic, so their results are equal bit for
+// bit, and the handle picks the faster one by timing both (mpr_set_sweep_kernel).
+//
+// Templated on PROP (bounded Metropolis proposals): mpr_sweep_f32.cu instantiates the uniform
+// proposal variants, mpr_sweep_f32_prop.cu the bounded ones, so the two compile in parallel.
+#pragma once
+#include "mpr_tile_f32.cuh"
+
+namespace mpr {
+namespace sweep_f32_detail {
+
+using namespace f32;
+
+constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
+
+// Compiled for 4 resident blocks per SM (64 registers: no spills with 16-bit spins, a few bytes
+// with FP32 spins in the energy and sampling variants); 2 for FP64 spins, whose values take
+// twice the registers and would spill at 3 or 4. Bounded proposals keep the old angle and the
+// half-width live across the move: 3 blocks per SM, without spills.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : (PROP ? 3 : 4))
+    sweep_f32_kernel(const SweepArgs a)
+{
+    static_assert(R % 2 == 0, "the 64-column tail tile has R / 2 rows per thread");
+    __shared__ __align__(16) TileSmem<R> sm;
+    // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
+    const int b = blockIdx.x;
+    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    const int tx = b % ntx, ty = b / ntx;
+    void* eslot = nullptr;
+    if (MEASURE)
+        eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
+    // a last tile column of at most 64 columns runs as a 64-column tile of the same height (tile
+    // column 2 tx in 64-column units), as the batched kernels do: the energy partials, and so the
+    // energies, stay bit-identical between the two paths
+    if (tx == ntx - 1 && a.Lxh - tx * kTJ <= 64)
+        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64>(
+            a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
+    else
+        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP>(a, tx, ty, sm, eslot);
+}
+
+// Launched as a programmatic dependent launch: while the previous pass's last blocks finish, this
+// pass's blocks are scheduled and load their own rows (see sweep_tile).
+template <typename S, bool MEASURE, int SAMPLE, bool PROP>
+cudaError_t go(const SweepArgs& a, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>()));
+    cfg.blockDim = dim3(32, kWarps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_f32_kernel<S, kRows, MEASURE, SAMPLE, PROP>, a);
+}
+
+template <typename S, bool PROP>
+cudaError_t dispatch_mode(const Precision& p, const SweepArgs& a, cudaStream_t st)
+{
+    const bool measure = (a.flags & kMeasure) && a.colour == 1;
+    const int sample = (a.flags & kSample) ? (p.acc == 0 ? 1 : 2) : 0;
+    if (measure) {
+        if (sample == 0) return go<S, true, 0, PROP>(a, st);
+        if (sample == 1) return go<S, true, 1, PROP>(a, st);
+        return go<S, true, 2, PROP>(a, st);
+    }
+    if (sample == 0) return go<S, false, 0, PROP>(a, st);
+    if (sample == 1) return go<S, false, 1, PROP>(a, st);
+    return go<S, false, 2, PROP>(a, st);
+}
+
+template <bool PROP>
+cudaError_t launch_store(const Precision& p, const SweepArgs& a, cudaStream_t st)
+{
+    switch (p.store) {
+    case kF64: return dispatch_mode<double, PROP>(p, a, st);
+    case kF32: return dispatch_mode<float, PROP>(p, a, st);
+    case kF16: return dispatch_mode<__half, PROP>(p, a, st);
+    case kBF16: return dispatch_mode<__nv_bfloat16, PROP>(p, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sweep_f32_detail
+}  // namespace mpr

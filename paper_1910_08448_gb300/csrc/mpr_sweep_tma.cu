@@ -129,13 +129,14 @@ __global__ void __launch_bounds__(256, 3)
 
         double e_d = 0.0;   // unused: no energy in plain passes
         float e_f = 0.0f;
+        int n_acc = 0;      // unused: uniform proposals only
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int ly = warp * R + row_of<R>(i, a.colour);
             const int y = y0 + ly;
             if (y < a.Ly)
-                update_row_i<S, R, false, 0, true>(i, a, y, ly, jb, lj, mine[i], bits[i], sm.t, e_d,
-                                                   e_f);
+                update_row_i<S, R, false, 0, true, false>(i, a, y, ly, jb, lj, mine[i], bits[i], sm.t,
+                                                          e_d, e_f, 0.0f, n_acc);
         }
         if (leader && tn < ntiles) await(it + 1);
         __syncthreads();   // the unit vectors' readers are done; sm.ok is current

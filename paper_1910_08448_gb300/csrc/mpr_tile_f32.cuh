@@ -204,11 +204,12 @@ template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, fl
 // none, 1 FP64 accumulators, 2 Kahan FP32 accumulators. MEASURE adds u_b . h_b of the row's
 // existing (black) sites to e_d or e_f. SCHED: Philox words from the precomputed schedule a.ph
 // (a kernel parameter) instead of the seed. OPAR: the row's column offset o = (y + colour) & 1
-// when the caller knows it at compile time (0 or 1), else -1.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, int TJ>
+// when the caller knows it at compile time (0 or 1), else -1. PROP: bounded proposals
+// f + pw (2u - 1), rejected outside [0, 2 pi); n_acc counts the accepted ones of updated sites.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, int TJ>
 __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
                                            Pack4<S>& pk, uint32_t bits, const TileSmem<R, TJ>& sm,
-                                           double& e_d, float& e_f)
+                                           double& e_d, float& e_f, float pw, int& n_acc)
 {
     const int c = a.colour;
     S* __restrict__ own = static_cast<S*>(a.own);
@@ -272,14 +273,23 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             const uint32_t wp = (k & 1) ? w.z : w.x;
             const uint32_t wa = (k & 1) ? w.w : w.y;
             const float u_acc = uniform_f(wa);
-            // Metropolis: uniform proposal fp = 2 pi u, accept if dE <= 0 or u_acc < exp(-dE/T)
-            const float fp = fmaf(two_pi, one_plus_uniform_f(wp), -two_pi);
+            // Metropolis: uniform proposal fp = 2 pi u (or bounded: f + pw (2u - 1), inside
+            // [0, 2 pi) only), accept if dE <= 0 or u_acc < exp(-dE/T)
+            float fp;
+            bool inside = true;
+            if constexpr (PROP) {
+                fp = fmaf(2.0f * pw, uniform_f(wp), f - pw);
+                inside = fp >= 0.0f && fp < two_pi;
+            } else {
+                fp = fmaf(two_pi, one_plus_uniform_f(wp), -two_pi);
+            }
             float s0, c0, sp, cp;
             __sincosf(q * f, &s0, &c0);
             __sincosf(q * fp, &sp, &cp);
             // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
             const float dE = hxk * (c0 - cp) + hyk * (s0 - sp);
-            const bool accept = dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT);
+            const bool accept = inside && (dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT));
+            if constexpr (PROP) n_acc += (accept && upd[k]) ? 1 : 0;
             const float f1 = accept ? fp : f;
             // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
             // h = 0 gives NaN in atan2_doubled, every comparison below is false and the angle
@@ -377,17 +387,31 @@ template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R
 
 // update_row of the i-th row in the order row_of(), with o fixed at compile time for even R (the
 // branch on i & 1 disappears when the caller's loop over i is unrolled).
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int TJ>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, int TJ>
 __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
                                              int lj, Pack4<S>& pk, uint32_t bits,
-                                             const TileSmem<R, TJ>& sm, double& e_d, float& e_f)
+                                             const TileSmem<R, TJ>& sm, double& e_d, float& e_f,
+                                             float pw, int& n_acc)
 {
     if constexpr (R % 2 == 0) {
-        if (i & 1) update_row<S, R, MEASURE, SAMPLE, SCHED, 1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
-        else update_row<S, R, MEASURE, SAMPLE, SCHED, 0>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
+        if (i & 1)
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d,
+                                                              e_f, pw, n_acc);
+        else
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d,
+                                                              e_f, pw, n_acc);
     } else {
-        update_row<S, R, MEASURE, SAMPLE, SCHED, -1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f);
+        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f,
+                                                           pw, n_acc);
     }
+}
+
+// Adds the block's accepted bounded proposals to *counter: one atomic per warp.
+__device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* counter)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, off);
+    if (threadIdx.x == 0 && n_acc) atomicAdd(counter, (unsigned long long)n_acc);
 }
 
 // One tile (tile column tx, tile row ty) of colour a.colour, staged from global memory. With
@@ -399,7 +423,9 @@ __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, i
 // has completed: the previous pass's blocks released this pass only after their own wait.
 // Everything the previous pass may write (the other colour, accumulators, energy partials) is
 // touched only after the wait.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false, int TJ = kTJ>
+// PROP: bounded proposals of half-width *a.width; accepted ones counted into *a.accepted.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false,
+          bool PROP = false, int TJ = kTJ>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
@@ -442,13 +468,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
 
     double e_d = 0.0;
     float e_f = 0.0f;
+    const float pw = PROP ? (float)*a.width : 0.0f;   // written before this pass (stream order)
+    int n_acc = 0;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int ly = row0 + row_of<R>(i, c);
         const int y = y0 + ly;
         if (y < a.Ly)
-            update_row_i<S, R, MEASURE, SAMPLE, SCHED>(i, a, y, ly, jb, lj, mine[i], bits[i], sm, e_d, e_f);
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP>(i, a, y, ly, jb, lj, mine[i], bits[i],
+                                                             sm, e_d, e_f, pw, n_acc);
     }
+    if (PROP && a.accepted) count_accepted(n_acc, a.accepted);
     if (MEASURE) tile_energy(a, e_d, e_f, sm, eslot);
 }
 

@@ -382,6 +382,31 @@ def test_device_entry_points(mpr):
         mpr.mpr_destroy(h2)
 
 
+def test_problem_class_equals_the_c_calls(mpr):
+    # the convenience class (host and device inputs) runs the same chain as the plain calls
+    import torch
+
+    pr = mpr_inputs.make_problem(120, 90, 0.66, field_seed=21, mask_seed=22)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, "HDS", seed=4)
+        T, _ = mpr.mpr_tune_temperature(h)
+        mpr.mpr_run(h, 30, 10)
+        ref = mpr.mpr_predict(h)
+    finally:
+        mpr.mpr_destroy(h)
+    with mpr.Problem(pr.z, pr.mask, setup="HDS", seed=4) as p:
+        assert p.tune() == T
+        p.run(30, 10)
+        assert np.array_equal(p.predict(), ref)
+    zt = torch.from_numpy(pr.z).cuda()
+    mt = torch.from_numpy(pr.mask).cuda()
+    with mpr.GapFiller(zt, mt, setup="HDS", seed=4) as p:
+        assert np.array_equal(p.fill(30, 10), ref) and p.T == T
+        out = p.predict(torch.empty_like(zt))
+        assert np.array_equal(out.cpu().numpy(), ref)
+
+
 # --- checkpoint / resume and other q -------------------------------------------------------
 
 @pytest.mark.parametrize("setup", ["DDD", "SDS", "HDS"])

@@ -1,0 +1,191 @@
+"""Bounded Metropolis proposals with an adapted half-width, GPU against the oracle.
+
+The proposal phi' = phi + w (2u - 1), rejected outside [0, 2 pi), is symmetric, so the
+acceptance rule of the hybrid step (Sec. 2) is unchanged; the oracle pins show that it samples the
+same conditional Gibbs measure. Here: one sweep from an identical state and Philox stream through
+every kernel family (FP64 generic kernel, FP32 tile kernel with FP32 and 16-bit storage), and the
+width adaptation w <- w exp(a - target) step by step (DDD) and in its outcome (FP32).
+Tolerances and margins follow the uniform-proposal parity tests: a site whose Metropolis margin,
+over-relaxation margin or distance of the proposal from the ends of [0, 2 pi) is below the
+threshold is excused, with the black neighbours of such red sites.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mpr_inputs
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2.0 * math.pi
+
+
+@pytest.fixture(scope="module")
+def mpr():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_08448_gb300 as m
+
+    m.load()
+    return m
+
+
+def _round_store(a, setup):
+    if setup[0] == "H":
+        return np.asarray(a, np.float16).astype(np.float64)
+    if setup[0] == "S":
+        return np.asarray(a, np.float32).astype(np.float64)
+    return np.asarray(a, np.float64)
+
+
+def _colour(Lx, Ly):
+    return (np.arange(Ly)[:, None] + np.arange(Lx)[None, :]) % 2
+
+
+def _neighbours(b):
+    out = np.zeros_like(b)
+    out[:, 1:] |= b[:, :-1]
+    out[:, :-1] |= b[:, 1:]
+    out[1:, :] |= b[:-1, :]
+    out[:-1, :] |= b[1:, :]
+    return out
+
+
+def _start(orc, pr, setup, seed, width):
+    o = orc.Oracle(pr.Lx, pr.Ly, seed=seed, ubits=32 if setup[2] == "D" else 23, width=width)
+    phi, _, _ = o.map(pr.z, pr.mask)
+    rng = np.random.default_rng(seed)
+    state = np.where(pr.mask == 1, phi, rng.random(pr.z.shape) * TWO_PI)
+    return o, _round_store(state, setup)
+
+
+def _gpu(mpr, pr, setup, seed, state, sweep, T, width, target, n, kernel=-1):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=seed)
+        if kernel >= 0:
+            mpr.mpr_set_sweep_kernel(h, kernel)
+        mpr.mpr_set_proposal(h, width, target)
+        mpr.mpr_set_state(h, state, sweep)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, n, 0)
+        got, sw = mpr.mpr_get_state(h)
+        w = mpr.mpr_get_proposal(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    return got, sw, w, info
+
+
+# Shapes: one tile, a ragged tile row and column (the 64-column tail tile at 300 x 45), several
+# tiles per dimension.
+@pytest.mark.parametrize("Lx,Ly,p", [(131, 37, 0.9), (300, 45, 0.66), (1100, 300, 0.9)])
+@pytest.mark.parametrize("width", [0.4, 2.5])
+@pytest.mark.parametrize("setup", ["DDD", "SDS"])
+def test_bounded_single_sweep(mpr, orc, Lx, Ly, p, width, setup):
+    T = 0.3
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=11, mask_seed=12)
+    o, state = _start(orc, pr, setup, 21, width)
+    got, sw, w, info = _gpu(mpr, pr, setup, 21, state, 5, T, width, 0.0, 1)
+    exp, mm, om = o.sweep(state, pr.mask, T, 5, margins=True)
+    assert sw == 6 and w == width
+    assert info["sweep_kernel"] == (-1 if setup == "DDD" else 0)
+    thr, tol = (1e-11, 1e-9) if setup == "DDD" else (1e-4, 1e-4)
+    bad = (mm < thr) | (om < thr)
+    col = _colour(Lx, Ly)
+    excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
+    d = np.abs(got - exp)
+    assert np.all(d[~excused] <= tol), d[~excused].max()
+    assert excused.sum() <= max(3, 2e-3 * Lx * Ly)
+    m = pr.mask == 1
+    assert np.array_equal(got[m], state[m])
+
+
+@pytest.mark.parametrize("Lx,Ly,p", [(300, 45, 0.66), (1100, 300, 0.9)])
+def test_bounded_single_sweep_fp16(mpr, orc, Lx, Ly, p):
+    # 16-bit storage: the red half against the oracle's red half-sweep (identical inputs)
+    T, width = 0.5, 1.0
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=13, mask_seed=14)
+    o, state = _start(orc, pr, "HDS", 22, width)
+    got, _, _, _ = _gpu(mpr, pr, "HDS", 22, state, 9, T, width, 0.0, 1)
+    red, mm, om = o.half_sweep(state, pr.mask, T, 9, 0)
+    sel = (_colour(Lx, Ly) == 0) & (mm >= 1e-4) & (om >= 1e-4)
+    d = np.abs(got - _round_store(red, "HDS"))
+    assert np.all(d[sel] <= 2.0**-8 + 1e-4), d[sel].max()
+
+
+def test_bounded_proposal_forces_the_tile_kernel(mpr, orc):
+    # the TMA kernel draws uniform proposals only: a forced kind 1 runs kind 0 while the bounded
+    # proposal is on, and the result is the tile kernel's
+    pr = mpr_inputs.make_problem(600, 80, 0.9, field_seed=15, mask_seed=16)
+    _, state = _start(orc, pr, "HDS", 23, 1.5)
+    a, _, _, i1 = _gpu(mpr, pr, "HDS", 23, state, 0, 0.4, 1.5, 0.0, 2, kernel=1)
+    b, _, _, i0 = _gpu(mpr, pr, "HDS", 23, state, 0, 0.4, 1.5, 0.0, 2, kernel=0)
+    assert i1["sweep_kernel"] == 0 and i0["sweep_kernel"] == 0
+    assert np.array_equal(a, b)
+
+
+def test_adaptive_width_matches_oracle_ddd(mpr, orc):
+    # the same chain on both sides: states sweep by sweep and the width after every sweep follow
+    # the oracle's run; a rare accept decision within rounding of its threshold may differ
+    pr = mpr_inputs.make_problem(96, 64, 0.66, field_seed=17, mask_seed=18)
+    T, target, n = 0.05, 0.5, 30
+    o, state = _start(orc, pr, "DDD", 24, TWO_PI)
+    exp, widths = o.run_adapt(state, pr.mask, T, 0, n, target)
+    got, sw, w, info = _gpu(mpr, pr, "DDD", 24, state, 0, T, TWO_PI, target, n)
+    assert sw == n
+    assert widths[-1] < 0.5 * TWO_PI            # the width did adapt
+    assert abs(w / o.cfg.width - 1.0) < 1e-3, (w, o.cfg.width)
+    d = np.abs(got - exp)[pr.mask == 0]
+    assert np.mean(d < 1e-6) > 0.99, np.sort(d)[-10:]
+
+
+@pytest.mark.parametrize("setup", ["HDS", "SDS"])
+def test_adaptive_width_fp32_settles_like_the_oracle(mpr, orc, setup):
+    # FP32 functions: not the same chain as the FP64 oracle, but the width the adaptation settles
+    # on is a property of the conditional measure at T: both land within the fluctuation
+    pr = mpr_inputs.make_problem(256, 128, 0.9, field_seed=19, mask_seed=20)
+    T, target, n = 0.05, 0.4, 300
+    o, state = _start(orc, pr, setup, 25, TWO_PI)
+    _, widths = o.run_adapt(state, pr.mask, T, 0, n, target)
+    w_orc = float(np.mean(widths[-50:]))
+    ws = []
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=25)
+        mpr.mpr_set_proposal(h, TWO_PI, target)
+        mpr.mpr_set_state(h, state, 0)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, n - 50, 0)
+        for _ in range(50):
+            mpr.mpr_run(h, 1, 0)
+            ws.append(mpr.mpr_get_proposal(h))
+        # sampling sweeps hold the width
+        w0 = mpr.mpr_get_proposal(h)
+        mpr.mpr_run(h, 0, 5)
+        assert mpr.mpr_get_proposal(h) == w0
+        # back to uniform proposals
+        mpr.mpr_set_proposal(h, 0.0, 0.0)
+        assert mpr.mpr_get_proposal(h) == 0.0
+    finally:
+        mpr.mpr_destroy(h)
+    w_gpu = float(np.mean(ws))
+    assert w_gpu < 0.5 * TWO_PI
+    assert abs(w_gpu / w_orc - 1.0) < 0.15, (w_gpu, w_orc)
+
+
+def test_proposal_arguments(mpr):
+    pr = mpr_inputs.make_problem(40, 30, 0.5, field_seed=1, mask_seed=2)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        for w, t in [(-0.1, 0.0), (7.0, 0.0), (1.0, 1.0), (1.0, -0.5), (float("nan"), 0.0)]:
+            with pytest.raises(mpr.MPRError) as ei:
+                mpr.mpr_set_proposal(h, w, t)
+            assert ei.value.status == mpr.MPR_ERR_INVALID_ARG
+        assert mpr.mpr_get_proposal(h) == 0.0
+        mpr.mpr_set_proposal(h, TWO_PI, 0.3)
+        assert mpr.mpr_get_proposal(h) == TWO_PI
+    finally:
+        mpr.mpr_destroy(h)

@@ -111,3 +111,66 @@ def test_config3_16bit_storage_vs_fp64_gpu(mpr, setup, acc):
     print(f"\nconfig 3 {setup}/{acc} vs DDD: MAE {mh:.4f} vs {md:.4f} ({mh / md - 1:.2e}), "
           f"RMSE gap {rh / rd - 1:.2e}, e_bond gap {eh / ed - 1:.2e}")
     assert abs(mh / md - 1.0) < 0.01 and abs(rh / rd - 1.0) < 0.01 and abs(eh / ed - 1.0) < 0.01
+
+
+def _job_from(mpr, pr, setup, seed, T, equil, samples, start=None, proposal=None):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=seed)
+        if start is not None:
+            mpr.mpr_set_state(h, start, 0)
+        if proposal is not None:
+            mpr.mpr_set_proposal(h, *proposal)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, equil, samples)
+        zhat = mpr.mpr_predict(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    return zhat, info["e_bond_mean"]
+
+
+def _tuned_T(mpr, pr, setup, seed):
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        mpr.mpr_set_options(h, setup, seed=seed)
+        T, _ = mpr.mpr_tune_temperature(h)
+    finally:
+        mpr.mpr_destroy(h)
+    return T
+
+
+def test_equilibrium_does_not_depend_on_the_start(mpr):
+    # Sec. 2 averages equilibrium configurations: a hot start (uniform angles) and a cold start
+    # (every prediction site at the mean measured angle) give the same predictions and energy
+    gaps = []
+    for s in range(3):
+        pr = mpr_inputs.make_problem(256, 256, 0.66, field_seed=40 + s, mask_seed=50 + s)
+        T = _tuned_T(mpr, pr, "SDS", s)
+        h = mpr.mpr_create(pr.z, pr.mask)
+        try:
+            hot, _ = mpr.mpr_get_state(h)
+        finally:
+            mpr.mpr_destroy(h)
+        cold = np.where(pr.mask == 1, hot, hot[pr.mask == 1].mean())
+        zh, eh = _job_from(mpr, pr, "SDS", s, T, 2000, 200)
+        zc, ec = _job_from(mpr, pr, "SDS", s, T, 2000, 200, start=cold)
+        gaps.append((_metrics(zc, pr)[0] / _metrics(zh, pr)[0] - 1.0, ec / eh - 1.0))
+    g = np.mean(np.array(gaps), axis=0)
+    print(f"\ncold vs hot start: MAE gap {g[0]:.2e}, e_bond gap {g[1]:.2e}")
+    assert abs(g[0]) < 0.01 and abs(g[1]) < 0.01
+
+
+@pytest.mark.parametrize("setup", ["SDS", "HDS"])
+def test_bounded_proposals_give_the_same_predictions(mpr, setup):
+    # the adapted-width proposal samples the same conditional measure as the uniform one
+    gaps = []
+    for s in range(3):
+        pr = mpr_inputs.make_problem(256, 256, 0.9, field_seed=60 + s, mask_seed=70 + s)
+        T = _tuned_T(mpr, pr, setup, s)
+        zu, eu = _job_from(mpr, pr, setup, s, T, 1500, 200)
+        zb, eb = _job_from(mpr, pr, setup, s, T, 1500, 200, proposal=(2.0 * np.pi, 0.4))
+        gaps.append((_metrics(zb, pr)[0] / _metrics(zu, pr)[0] - 1.0, eb / eu - 1.0))
+    g = np.mean(np.array(gaps), axis=0)
+    print(f"\n{setup} bounded vs uniform proposals: MAE gap {g[0]:.2e}, e_bond gap {g[1]:.2e}")
+    assert abs(g[0]) < 0.01 and abs(g[1]) < 0.01
