@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="batch: default launch shape")
     ap.add_argument("--sweep-kernel", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP32 sweep kernel: -1 automatic (timed per job), 0 tile per block, 1 TMA-fed")
+    ap.add_argument("--proposal", default="",
+                    help="bounded Metropolis proposals 'WIDTH,TARGET' (mpr_set_proposal); default uniform")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -250,6 +252,7 @@ def run_mine(args, dist: Dist):
     out = torch.empty_like(zt)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     seed = 7 + dist.rank
+    proposal = tuple(float(v) for v in args.proposal.split(",")) if args.proposal else None
 
     def step_device(profile=False):
         h = mpr.mpr_create_dev(zt, mt)
@@ -257,6 +260,8 @@ def run_mine(args, dist: Dist):
             mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
             if args.sweep_kernel >= 0:
                 mpr.mpr_set_sweep_kernel(h, args.sweep_kernel)
+            if proposal:
+                mpr.mpr_set_proposal(h, *proposal)
             mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
             if profile:
                 mpr.mpr_set_profiling(h, True)
@@ -315,7 +320,7 @@ def run_mine(args, dist: Dist):
     t_hbm = bytes_launch / (hbm_gbs * 1e9)
     kname = SWEEP_KERNELS[infos[-1]["sweep_kernel"]]
     kid = sweep_kernel_id(kname)
-    workload = f"L{L}_p{p}_{args.setup}"
+    workload = f"L{L}_p{p}_{args.setup}" + ("_bounded" if proposal else "")
     traffic = stored_traffic(kid, kname, workload)
     if t_hbm >= t_mufu:
         roof = {"bound": "hbm", "achieved": bytes_launch / t_launch / 1e9, "peak": hbm_gbs,
@@ -374,6 +379,8 @@ def run_mine(args, dist: Dist):
                 mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
                 if args.sweep_kernel >= 0:
                     mpr.mpr_set_sweep_kernel(h, args.sweep_kernel)
+                if proposal:
+                    mpr.mpr_set_proposal(h, *proposal)
                 mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
                 mpr.mpr_tune_temperature(h)
                 mpr.mpr_run(h, args.equil, args.samples)
@@ -517,6 +524,8 @@ def main():
               "acc": args.acc, "equil": args.equil, "samples": args.samples,
               "tune_probe_sweeps": [args.tune_eq, args.tune_meas],
               "l2": "flushed between steps (512 MB write)"}
+    if args.proposal:
+        config["proposal"] = args.proposal   # bounded Metropolis proposals: width, target
 
     if args.impl == "reference":
         if dist.rank == 0:

@@ -124,6 +124,27 @@ mpr_status mpr_set_tuning(mpr_handle h, const mpr_tuning* t);
 mpr_status mpr_tune_temperature(mpr_handle h, double* T_out);
 mpr_status mpr_set_temperature(mpr_handle h, double T);   /* T > 0; bypasses the tuning */
 
+/* Alternative tunings (readings of Sec. 2, which says only that T is inferred from the data).
+ *
+ * Heating: probe T_lo, then T *= factor per probe (clamped to T_hi; the chain carries over, so
+ * every probe starts from the cooler probe's equilibrium) until e_b(T) passes e_s, then bisection
+ * in log T inside the last bracket with the stopping rules of mpr_tune_temperature. e_s at or
+ * below e_b(T_lo): T_lo. No crossing up to T_hi, or max_probes reached: TUNE_NO_CONVERGE with T
+ * set to the last temperature (or bracket midpoint). factor in (1, 100], else INVALID_ARG. */
+mpr_status mpr_tune_heating(mpr_handle h, double factor, double* T_out);
+/* Energy curve of the unconditional model: an Lx x Ly lattice with every site free (no data),
+ * uniform random start, options `opt` (NULL: defaults; seed, q, precision), then for each T[i] in
+ * turn n_eq sweeps and the mean bond energy e_b over n_meas sweeps (from `tuning`; NULL:
+ * defaults), the chain carrying over between temperatures. e_out: n doubles (host). Runs on the
+ * legacy default stream and synchronises; allocates and frees its own device memory. */
+mpr_status mpr_energy_curve(int Lx, int Ly, const mpr_options* opt, const mpr_tuning* tuning,
+                            const double* T, int n, double* e_out);
+/* Sets T from a tabulated curve e(T) (host arrays, n >= 2, T increasing): the temperature where
+ * the piecewise-linear interpolant in log T first reaches the handle's e_s. e_s at or below e[0]:
+ * T[0]; above every e[i]: T[n-1] with TUNE_NO_CONVERGE. No sweeps run. */
+mpr_status mpr_tune_from_curve(mpr_handle h, const double* T, const double* e, int n,
+                               double* T_out);
+
 /* equil sweeps, then samples sweeps after each of which every prediction angle is added to its
  * accumulator (Sec. 2: averaging over configurations in equilibrium). One hybrid sweep updates
  * all red prediction sites, then all black ones; each update is a Metropolis move with a uniform

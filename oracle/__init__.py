@@ -102,6 +102,13 @@ def lib():
             L.mpro_run.restype = None
             L.mpro_tune.argtypes = [P(Cfg), vp, vp, d, P(u32), P(TuneCfg), P(d), vp, vp, P(i)]
             L.mpro_tune.restype = i
+            L.mpro_tune_heating.argtypes = [P(Cfg), vp, vp, d, P(u32), P(TuneCfg), d, P(d), vp,
+                                            vp, P(i)]
+            L.mpro_tune_heating.restype = i
+            L.mpro_energy_curve.argtypes = [P(Cfg), vp, i, P(TuneCfg), P(u32), vp]
+            L.mpro_energy_curve.restype = None
+            L.mpro_invert_curve.argtypes = [vp, vp, i, d, P(d)]
+            L.mpro_invert_curve.restype = i
             L.mpro_equilibrate.argtypes = [P(Cfg), vp, vp, d, P(u32), i, i, d]
             L.mpro_equilibrate.restype = i
             L.mpro_predict.argtypes = [i, vp, i, vp, vp, d, d, vp]
@@ -127,6 +134,14 @@ def overrelax(q: float, hx: float, hy: float, phi: float):
     m = ctypes.c_double()
     f = lib().mpro_overrelax(q, hx, hy, phi, ctypes.byref(m))
     return f, m.value
+
+
+def invert_curve(T, e, e_s):
+    """(status, T) where the log-T interpolant of the tabulated curve e(T) reaches e_s."""
+    T, e = _f64(T), _f64(e)
+    out = ctypes.c_double()
+    st = lib().mpro_invert_curve(_ptr(T), _ptr(e), T.size, e_s, ctypes.byref(out))
+    return st, out.value
 
 
 def philox(width: int, rounds: int, ctr, key) -> np.ndarray:
@@ -265,6 +280,33 @@ class Oracle:
                              ctypes.byref(t), ctypes.byref(T), _ptr(tT), _ptr(te), ctypes.byref(n))
         trace = list(zip(tT[: n.value].tolist(), te[: n.value].tolist()))
         return st, T.value, phi, sw.value, trace
+
+    def tune_heating(self, phi, mask, e_s, sweep, factor=1.5, n_eq=200, n_meas=50, T_lo=1e-3,
+                     T_hi=10.0, rel_tol=1e-3, ratio_tol=1.001, max_probes=30):
+        """Heating tuning: returns (status, T, phi, next_sweep, trace) like tune()."""
+        phi = _f64(phi).copy()
+        m = _u8(mask)
+        t = TuneCfg(n_eq, n_meas, T_lo, T_hi, rel_tol, ratio_tol, max_probes)
+        sw = ctypes.c_uint32(sweep)
+        T = ctypes.c_double()
+        tT = np.zeros(max_probes)
+        te = np.zeros(max_probes)
+        n = ctypes.c_int()
+        st = lib().mpro_tune_heating(ctypes.byref(self.cfg), _ptr(phi), _ptr(m), e_s,
+                                     ctypes.byref(sw), ctypes.byref(t), factor, ctypes.byref(T),
+                                     _ptr(tT), _ptr(te), ctypes.byref(n))
+        trace = list(zip(tT[: n.value].tolist(), te[: n.value].tolist()))
+        return st, T.value, phi, sw.value, trace
+
+    def energy_curve(self, T, n_eq=200, n_meas=50, sweep=0):
+        """Mean e_b of the unconditional lattice (no frozen site) at each T in turn."""
+        T = _f64(T)
+        e = np.zeros(max(T.size, 1))
+        t = TuneCfg(n_eq, n_meas, 1e-3, 10.0, 1e-3, 1.001, 30)
+        sw = ctypes.c_uint32(sweep)
+        lib().mpro_energy_curve(ctypes.byref(self.cfg), _ptr(T), T.size, ctypes.byref(t),
+                                ctypes.byref(sw), _ptr(e))
+        return e[: T.size]
 
     def equilibrate(self, phi, mask, T, sweep, chunk, max_sweeps, z=2.0):
         """Energy-slope equilibration: returns (phi, sweeps run, next sweep)."""

@@ -444,6 +444,92 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Alternative tunings. Readings, not the paper's (Sec. 2 says only that the temperature is     */
+/* inferred from the incomplete data).                                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Heating: probe T_lo, then raise T by `factor` per probe (the chain carries over, so each probe
+ * starts from the equilibrium of the cooler one) until e_b(T) reaches e_s; the last two
+ * temperatures bracket the crossing, which bisection in log T then refines with the stopping
+ * rules of mpro_tune. No crossing up to T_hi: status 4 with T = T_hi. */
+int mpro_tune_heating(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double e_s,
+                      uint32_t* sweep, const mpro_tune_cfg* t, double factor, double* T_out,
+                      double* trace_T, double* trace_e, int* n_probes)
+{
+    const double tol = t->rel_tol * fabs(e_s);
+    int np = 0;
+    int status = 0;
+    double T = t->T_lo, e, lo, hi;
+
+    e = probe(cfg, phi, mask, sweep, t, T);
+    if (trace_T) { trace_T[np] = T; trace_e[np] = e; }
+    ++np;
+    if (fabs(e - e_s) <= tol || e_s < e) { *T_out = T; goto done; }
+
+    /* heat until the energy passes e_s */
+    for (;;) {
+        if (T >= t->T_hi) { *T_out = T; status = 4; goto done; }
+        if (np >= t->max_probes) { *T_out = T; status = 4; goto done; }
+        double Tn = T * factor;
+        if (Tn > t->T_hi) Tn = t->T_hi;
+        e = probe(cfg, phi, mask, sweep, t, Tn);
+        if (trace_T) { trace_T[np] = Tn; trace_e[np] = e; }
+        ++np;
+        if (fabs(e - e_s) <= tol) { *T_out = Tn; goto done; }
+        if (e > e_s) { lo = log(T); hi = log(Tn); break; }
+        T = Tn;
+    }
+
+    /* bisection inside the bracket */
+    for (;;) {
+        if (hi - lo < log(t->ratio_tol)) { *T_out = exp(0.5 * (lo + hi)); goto done; }
+        if (np >= t->max_probes) { *T_out = exp(0.5 * (lo + hi)); status = 4; goto done; }
+        double mid = 0.5 * (lo + hi);
+        T = exp(mid);
+        e = probe(cfg, phi, mask, sweep, t, T);
+        if (trace_T) { trace_T[np] = T; trace_e[np] = e; }
+        ++np;
+        if (fabs(e - e_s) <= tol) { *T_out = T; goto done; }
+        if (e < e_s) lo = mid; else hi = mid;
+    }
+done:
+    if (n_probes) *n_probes = np;
+    return status;
+}
+
+/* Energy curve of the unconditional model: every site free, uniform start (mpro_init), then for
+ * each temperature in turn n_eq sweeps and the mean e_b over n_meas sweeps, the chain carrying
+ * over from one temperature to the next. The sweep counter starts at *sweep and advances. */
+void mpro_energy_curve(const mpro_cfg* cfg, const double* T, int n, const mpro_tune_cfg* t,
+                       uint32_t* sweep, double* e_out)
+{
+    const int N = cfg->Lx * cfg->Ly;
+    uint8_t* mask = (uint8_t*)calloc((size_t)N, 1);
+    double* phi = (double*)calloc((size_t)N, sizeof(double));
+    mpro_init(cfg, mask, phi);
+    for (int i = 0; i < n; ++i) e_out[i] = probe(cfg, phi, mask, sweep, t, T[i]);
+    free(phi);
+    free(mask);
+}
+
+/* Inverse of a tabulated curve e(T), T ascending: the temperature where the piecewise-linear
+ * interpolant in log T first reaches e_s. e_s at or below e[0]: T[0]; above every e[i]: T[n-1]
+ * with status 4. */
+int mpro_invert_curve(const double* T, const double* e, int n, double e_s, double* T_out)
+{
+    if (e_s <= e[0]) { *T_out = T[0]; return 0; }
+    for (int i = 1; i < n; ++i) {
+        if (e[i] >= e_s) {   /* here e[i-1] < e_s <= e[i] */
+            const double f = (e_s - e[i - 1]) / (e[i] - e[i - 1]);
+            *T_out = exp(log(T[i - 1]) + f * (log(T[i]) - log(T[i - 1])));
+            return 0;
+        }
+    }
+    *T_out = T[n - 1];
+    return 4;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Prediction: mean angle mapped back to the data scale (inverse of the mapping above).        */
 /* ------------------------------------------------------------------------------------------ */
 

@@ -102,6 +102,15 @@ int mpro_tune(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double e_s,
               const mpro_tune_cfg* tcfg, double* T_out, double* trace_T, double* trace_e,
               int* n_probes);
 
+/* Alternative tunings (readings): heating from T_lo by `factor` per probe until e_b crosses e_s,
+ * then bisection; the energy curve of the unconditional lattice; inversion of a tabulated curve. */
+int mpro_tune_heating(const mpro_cfg* cfg, double* phi, const uint8_t* mask, double e_s,
+                      uint32_t* sweep, const mpro_tune_cfg* t, double factor, double* T_out,
+                      double* trace_T, double* trace_e, int* n_probes);
+void mpro_energy_curve(const mpro_cfg* cfg, const double* T, int n, const mpro_tune_cfg* t,
+                       uint32_t* sweep, double* e_out);
+int mpro_invert_curve(const double* T, const double* e, int n, double e_s, double* T_out);
+
 /* Equilibration with an energy-slope stop (an option: the paper fixes no equilibration rule):
  * sweeps in chunks of `chunk` (>= 2), e_b recorded after every sweep; after the second and every
  * later chunk, stop when the chunk's mean differs from the previous chunk's by at most z standard

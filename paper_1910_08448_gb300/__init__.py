@@ -89,6 +89,9 @@ def load():
             "mpr_set_tuning": ([H, P(mpr_tuning)], i),
             "mpr_tune_temperature": ([H, P(d)], i),
             "mpr_set_temperature": ([H, d], i),
+            "mpr_tune_heating": ([H, d, P(d)], i),
+            "mpr_energy_curve": ([i, i, P(mpr_options), P(mpr_tuning), vp, i, vp], i),
+            "mpr_tune_from_curve": ([H, vp, vp, i, P(d)], i),
             "mpr_run": ([H, i, i], i),
             "mpr_run_auto": ([H, i, i, i, P(i)], i),
             "mpr_predict": ([H, vp], i),
@@ -131,6 +134,7 @@ def exported_symbols():
     """Names the binding expects the library to export (every function of include/mpr.h)."""
     return ["mpr_create", "mpr_create_dev", "mpr_destroy", "mpr_set_options", "mpr_get_options",
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
+            "mpr_tune_heating", "mpr_energy_curve", "mpr_tune_from_curve",
             "mpr_run", "mpr_run_auto", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
             "mpr_get_state", "mpr_set_state", "mpr_philox4x32_10_dev", "mpr_set_profiling",
             "mpr_set_sweep_kernel", "mpr_inject_tma_stall", "mpr_set_proposal", "mpr_get_proposal",
@@ -233,6 +237,38 @@ def mpr_tune_temperature(h):
     T = ctypes.c_double()
     st = _check(load().mpr_tune_temperature(h, ctypes.byref(T)), allow=(MPR_ERR_TUNE_NO_CONVERGE,))
     return T.value, st
+
+
+def mpr_tune_heating(h, factor: float = 1.5):
+    """Heating tuning: returns (T, status) like mpr_tune_temperature."""
+    T = ctypes.c_double()
+    st = load().mpr_tune_heating(h, float(factor), ctypes.byref(T))
+    _check(st, allow=(MPR_ERR_TUNE_NO_CONVERGE,))
+    return T.value, st
+
+
+def mpr_energy_curve(Lx: int, Ly: int, T, setup: str = "SDS", seed: int = 0, q: float = 0.5,
+                     n_eq: int = 200, n_meas: int = 50) -> np.ndarray:
+    """Mean bond energy of the unconditional Lx x Ly lattice at each temperature of T in turn."""
+    T = _f64_host(T).ravel()
+    e = np.empty_like(T)
+    opt = make_options(setup, seed, q)
+    tun = mpr_tuning(n_eq, n_meas, 1e-3, 10.0, 1e-3, 1.001, 30)
+    _check(load().mpr_energy_curve(int(Lx), int(Ly), ctypes.byref(opt), ctypes.byref(tun),
+                                   _ptr(T), T.size, _ptr(e)))
+    return e
+
+
+def mpr_tune_from_curve(h, T, e):
+    """Sets T by inverting the tabulated curve e(T): returns (T, status)."""
+    T = _f64_host(T).ravel()
+    e = _f64_host(e).ravel()
+    if T.size != e.size:
+        raise ValueError("T and e differ in length")
+    out = ctypes.c_double()
+    st = load().mpr_tune_from_curve(h, _ptr(T), _ptr(e), T.size, ctypes.byref(out))
+    _check(st, allow=(MPR_ERR_TUNE_NO_CONVERGE,))
+    return out.value, st
 
 
 def mpr_set_temperature(h, T: float):

@@ -91,6 +91,7 @@ struct mpr_ctx {
     long long N = 0, Np = 0, Nb = 0, Nss = 0;
     double zmin = 0, zmax = 0, e_s = 0, T = 0;
     bool have_T = false;
+    bool free_lattice = false;           // every site free (energy curve of the unconditional model)
     uint32_t sweep = 0;
     int nsamples = 0, n_probes = 0;
     double e_bond_mean = NAN;
@@ -290,22 +291,27 @@ mpr_status init_state(mpr_ctx* h)
     h->T = 0.0;
     h->n_probes = 0;
     h->e_bond_mean = NAN;
-    if (h->Nss == 0) return fail(MPR_ERR_NO_PAIRS, "no two measured sites are nearest neighbours");
+    if (h->Nss == 0 && !h->free_lattice)
+        return fail(MPR_ERR_NO_PAIRS, "no two measured sites are nearest neighbours");
     return MPR_OK;
 }
 
+// free_lattice: no data (values and mask ignored); every site is free, as in the unconditional
+// model whose energy curve mpr_energy_curve records.
 mpr_status create_common(int Lx, int Ly, const double* values, const unsigned char* mask,
-                         bool on_device, cudaStream_t stream, mpr_handle* out)
+                         bool on_device, cudaStream_t stream, mpr_handle* out,
+                         bool free_lattice = false)
 {
     if (!out) return fail(MPR_ERR_INVALID_ARG, "out pointer is NULL");
     *out = nullptr;
-    if (!values || !mask) return fail(MPR_ERR_INVALID_ARG, "values or mask is NULL");
+    if (!free_lattice && (!values || !mask)) return fail(MPR_ERR_INVALID_ARG, "values or mask is NULL");
     if (Lx < 2 || Ly < 2) return fail(MPR_ERR_INVALID_ARG, "grid %d x %d: both sides must be >= 2", Lx, Ly);
     if ((long long)Lx * Ly > 2147483647LL)
         return fail(MPR_ERR_INVALID_ARG, "grid %d x %d exceeds 2^31 - 1 sites", Lx, Ly);
     mpr_ctx* h = new (std::nothrow) mpr_ctx();
     if (!h) return fail(MPR_ERR_OOM, "host allocation failed");
     h->stream = stream;
+    h->free_lattice = free_lattice;
     h->opt = default_options();
     h->tune = default_tuning();
     h->prec = Precision{h->opt.store, h->opt.energy, h->opt.func, h->opt.acc};
@@ -345,6 +351,17 @@ mpr_status create_common(int Lx, int Ly, const double* values, const unsigned ch
     h->host[15] = 0.0;
     if ((s = dalloc(h, &h->z, (size_t)h->N * 8)) != MPR_OK) return bail(s);
     if ((s = dalloc(h, &h->mask, (size_t)h->N)) != MPR_OK) return bail(s);
+    if (free_lattice) {
+        if (cudaMemsetAsync(h->z, 0, (size_t)h->N * 8, stream) != cudaSuccess ||
+            cudaMemsetAsync(h->mask, 0, (size_t)h->N, stream) != cudaSuccess)
+            return bail(fail(MPR_ERR_CUDA, "lattice setup failed"));
+        h->zmin = 0.0;
+        h->zmax = 0.0;
+        h->Np = h->N;
+        if ((s = init_state(h)) != MPR_OK) return bail(s);
+        *out = h;
+        return MPR_OK;
+    }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(h->z, values, (size_t)h->N * 8, kind, stream) != cudaSuccess ||
         cudaMemcpyAsync(h->mask, mask, (size_t)h->N, kind, stream) != cudaSuccess)
@@ -614,6 +631,124 @@ done:
     h->have_T = true;
     h->n_probes = np;
     if (T_out) *T_out = T;
+    return status;
+}
+
+mpr_status mpr_tune_heating(mpr_handle h, double factor, double* T_out)
+{
+    NvtxRange r("mpr_tune_heating");
+    if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(factor > 1.0) || !(factor <= 100.0))
+        return fail(MPR_ERR_INVALID_ARG, "heating factor %g outside (1, 100]", factor);
+    if (h->free_lattice) return fail(MPR_ERR_STATE, "the lattice has no measured data");
+    const mpr_tuning& t = h->tune;
+    const double e_s = h->e_s;
+    const double tol = t.rel_tol * fabs(e_s);
+    int np = 0;
+    mpr_status status = MPR_OK;
+    double T = t.T_lo, e, lo = 0.0, hi = 0.0;
+
+    CHECK(probe(h, T, &e));
+    ++np;
+    if (fabs(e - e_s) <= tol || e_s < e) goto done;
+    // heat until the energy passes e_s (the chain carries over from probe to probe)
+    for (;;) {
+        if (T >= t.T_hi) {
+            status = fail(MPR_ERR_TUNE_NO_CONVERGE, "sample energy %.6f above e_b(T_hi) = %.6f", e_s, e);
+            goto done;
+        }
+        if (np >= t.max_probes) {
+            status = fail(MPR_ERR_TUNE_NO_CONVERGE, "no crossing in %d probes", np);
+            goto done;
+        }
+        const double Tn = std::min(T * factor, t.T_hi);
+        CHECK(probe(h, Tn, &e));
+        ++np;
+        if (fabs(e - e_s) <= tol) {
+            T = Tn;
+            goto done;
+        }
+        if (e > e_s) {
+            lo = log(T);
+            hi = log(Tn);
+            break;
+        }
+        T = Tn;
+    }
+    // bisection in log T inside the last bracket
+    for (;;) {
+        if (hi - lo < log(t.ratio_tol)) {
+            T = exp(0.5 * (lo + hi));
+            goto done;
+        }
+        if (np >= t.max_probes) {
+            T = exp(0.5 * (lo + hi));
+            status = fail(MPR_ERR_TUNE_NO_CONVERGE, "no convergence in %d probes", np);
+            goto done;
+        }
+        const double mid = 0.5 * (lo + hi);
+        T = exp(mid);
+        CHECK(probe(h, T, &e));
+        ++np;
+        if (fabs(e - e_s) <= tol) goto done;
+        if (e < e_s) lo = mid; else hi = mid;
+    }
+done:
+    h->T = T;
+    h->have_T = true;
+    h->n_probes = np;
+    if (T_out) *T_out = T;
+    return status;
+}
+
+mpr_status mpr_energy_curve(int Lx, int Ly, const mpr_options* opt, const mpr_tuning* tuning,
+                            const double* T, int n, double* e_out)
+{
+    NvtxRange r("mpr_energy_curve");
+    if (!T || !e_out || n < 1) return fail(MPR_ERR_INVALID_ARG, "NULL argument or n < 1");
+    for (int i = 0; i < n; ++i)
+        if (!(T[i] > 0.0) || !isfinite(T[i]))
+            return fail(MPR_ERR_INVALID_ARG, "temperature %d (%g) must be > 0", i, T[i]);
+    mpr_handle h = nullptr;
+    CHECK(create_common(Lx, Ly, nullptr, nullptr, false, nullptr, &h, true));
+    mpr_status s = opt ? mpr_set_options(h, opt) : MPR_OK;
+    if (s == MPR_OK && tuning) s = mpr_set_tuning(h, tuning);
+    for (int i = 0; i < n && s == MPR_OK; ++i) s = probe(h, T[i], &e_out[i]);
+    std::string keep = g_err;
+    mpr_destroy(h);
+    g_err = keep;
+    return s;
+}
+
+mpr_status mpr_tune_from_curve(mpr_handle h, const double* T, const double* e, int n, double* T_out)
+{
+    if (!h || !T || !e) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (n < 2) return fail(MPR_ERR_INVALID_ARG, "the curve needs at least 2 points (n = %d)", n);
+    for (int i = 0; i < n; ++i) {
+        if (!(T[i] > 0.0) || !isfinite(T[i]) || !isfinite(e[i]) || (i > 0 && !(T[i] > T[i - 1])))
+            return fail(MPR_ERR_INVALID_ARG, "point %d: T must be positive and increasing, e finite", i);
+    }
+    if (h->free_lattice) return fail(MPR_ERR_STATE, "the lattice has no measured data");
+    const double e_s = h->e_s;
+    mpr_status status = MPR_OK;
+    double Tc = T[n - 1];
+    if (e_s <= e[0]) {
+        Tc = T[0];
+    } else {
+        int i = 1;
+        while (i < n && e[i] < e_s) ++i;
+        if (i < n) {   // e[i - 1] < e_s <= e[i]: linear in log T
+            const double f = (e_s - e[i - 1]) / (e[i] - e[i - 1]);
+            Tc = exp(log(T[i - 1]) + f * (log(T[i]) - log(T[i - 1])));
+        } else {
+            status = fail(MPR_ERR_TUNE_NO_CONVERGE, "sample energy %.6f above the curve's top %.6f",
+                          e_s, e[n - 1]);
+        }
+    }
+    h->T = Tc;
+    h->have_T = true;
+    h->n_probes = 0;
+    if (T_out) *T_out = Tc;
     return status;
 }
 
