@@ -514,6 +514,90 @@ def oracle_sample(L, p, setup, seconds, seed=7, pr=None):
                       f"({n * n_pred} site-updates, {t:.1f} s, 1 thread)"}
 
 
+def _oracle_worker(args):
+    """One oracle replica for the all-cores sample: its own chain (seed) on the shared problem."""
+    zpath, mpath, L, setup, seed, n, barrier, queue = args
+    import numpy as np
+
+    import oracle
+
+    z = np.load(zpath)
+    mask = np.load(mpath)
+    o = oracle.Oracle(L, L, seed=seed, ubits=32 if setup[2] == "D" else 23)
+    phi, _, _ = o.map(z, mask)
+    phi = o.init(phi, mask)
+    n_pred = int((mask == 0).sum())
+    phi, _, _ = o.run(phi, mask, 0.5, 0, 1)   # warm-up sweep (page-in), untimed
+    barrier.wait()
+    t0 = time.monotonic()
+    o.run(phi, mask, 0.5, 1, n)
+    queue.put((n * n_pred, t0, time.monotonic()))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7):
+    """The oracle as it stands on every host core at once: one independent replica (own chain) per
+    process, all started together behind a barrier; value = all site-updates / the wall time from
+    the first start to the last finish (CLOCK_MONOTONIC is shared by the processes). Processes
+    are spawned, never forked, so a CUDA context in the parent is not inherited."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    single = oracle_sample(L, p, setup, min(seconds, 6.0), seed=seed, pr=pr)
+    workers = workers or host_cores()
+    # memory guard: each replica holds the data and about two copies of the state (FP64); use at
+    # most a quarter of the host's available memory
+    need = L * L * (3 * 8 + 1) + (64 << 20)
+    try:
+        with open("/proc/meminfo") as fh:
+            avail = next(int(ln.split()[1]) * 1024 for ln in fh if ln.startswith("MemAvailable:"))
+        workers = min(workers, max(1, int(0.25 * avail / need)))
+    except (OSError, StopIteration, ValueError):
+        workers = min(workers, 4)
+    if workers <= 1:
+        return single
+    # one replica's sweeps take about its single-thread time (more under memory contention)
+    n_pred = int((pr.mask == 0).sum())
+    t_sweep = n_pred / single["value"]
+    n = max(1, int(seconds / t_sweep / 2))
+    tmp = tempfile.mkdtemp(prefix="mpr_oracle_")
+    try:
+        zpath, mpath = os.path.join(tmp, "z.npy"), os.path.join(tmp, "mask.npy")
+        np.save(zpath, np.asarray(pr.z, np.float64))
+        np.save(mpath, np.asarray(pr.mask, np.uint8))
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(workers)
+        queue = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker,
+                             args=((zpath, mpath, L, setup, seed + 1 + i, n, barrier, queue),))
+                 for i in range(workers)]
+        for pr_ in procs:
+            pr_.start()
+        res = [queue.get(timeout=600) for _ in procs]
+        for pr_ in procs:
+            pr_.join(timeout=60)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    upd = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": upd / wall, "unit": "site-updates/s", "cores": workers, "kind": "oracle",
+            "sample": f"{workers} processes, each {n} hybrid sweeps of its own chain on the {L}x{L} "
+                      f"p={p} lattice at T=0.5 ({upd} site-updates in {wall:.1f} s wall)",
+            "single_thread": {"value": single["value"], "sample": single["sample"]}}
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -535,16 +619,20 @@ def main():
 
             pr = mpr_inputs.make_problem(args.L, args.L, args.p, field_seed=1, mask_seed=101)
             vals = []
-            for k in range(args.warmup + args.steps):
-                r = oracle_sample(args.L, args.p, args.setup, args.cpu_seconds / 2, pr=pr)
-                if k >= args.warmup:
-                    vals.append(r)
+            # warm-up steps: one single-thread sample each (pages the oracle and the data in)
+            for k in range(args.warmup):
+                oracle_sample(args.L, args.p, args.setup, 2.0, pr=pr)
+            for k in range(args.steps):
+                vals.append(oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds / 2,
+                                                pr))
             v = statistics.mean(r["value"] for r in vals)
             line = {"metric": metric, "value": v, "unit": "site-updates/s", "n_gpus": args.gpus,
                     "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                     "impl": "reference", "dtype": "f64", "data": "synthetic", "config": config,
-                    "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": 1,
-                                     "kind": "oracle", "sample": vals[-1]["sample"]},
+                    "cpu_baseline": {"value": v, "unit": "site-updates/s",
+                                     "cores": vals[-1]["cores"], "kind": "oracle",
+                                     "sample": vals[-1]["sample"],
+                                     "single_thread": vals[-1].get("single_thread")},
                     "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                             "d2h_bytes_per_step": 0},
                     "vs_baseline": None}
@@ -586,7 +674,7 @@ def main():
     res = run_mine(args, dist)
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
-        cpu = oracle_sample(args.L, args.p, args.setup, args.cpu_seconds, pr=res["problem"])
+        cpu = oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds, res["problem"])
     if dist.rank == 0:
         line = {
             "metric": metric, "value": res["value"], "unit": "site-updates/s",

@@ -76,6 +76,8 @@ def lib():
             vp = ctypes.c_void_p
             L.mpro_philox.argtypes = [i, i, vp, vp, vp]
             L.mpro_philox.restype = None
+            L.mpro_philox_n.argtypes = [i, i, i, vp, vp, vp]
+            L.mpro_philox_n.restype = None
             L.mpro_site_words.argtypes = [P(Cfg), i, i, u32, i, P(u32), P(u32)]
             L.mpro_site_words.restype = None
             L.mpro_uniform.argtypes = [P(Cfg), u32]
@@ -150,6 +152,15 @@ def philox(width: int, rounds: int, ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint64)
     out = np.zeros(4, dtype=np.uint64)
     lib().mpro_philox(width, rounds, _ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def philox_many(width: int, rounds: int, ctr, key) -> np.ndarray:
+    """The block function on an (n, 4) array of counters; returns (n, 4) uint64 words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros_like(c)
+    lib().mpro_philox_n(width, rounds, c.shape[0], _ptr(c), _ptr(k), _ptr(out))
     return out
 
 

@@ -76,6 +76,12 @@ void mpro_philox(int W, int rounds, const uint64_t ctr[4], const uint64_t key[2]
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+void mpro_philox_n(int W, int rounds, int n, const uint64_t* ctr, const uint64_t key[2],
+                   uint64_t* out)
+{
+    for (int i = 0; i < n; ++i) mpro_philox(W, rounds, ctr + 4 * (size_t)i, key, out + 4 * (size_t)i);
+}
+
 /* Counter layout (one Philox-4x32-10 call serves two same-colour sites of a row):
  *   ctr = (x >> 2, y, sweep, problem << 8 | tag << 1 | colour), key = (seed_lo, seed_hi);
  *   the site takes words 2t and 2t+1 with t = (x >> 1) & 1: the first word drives the

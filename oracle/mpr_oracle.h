@@ -45,6 +45,9 @@ typedef struct {
 /* Philox-NxW-R of Salmon et al. (SC'11), N = 4, W = 32 or 64. Counter, key and output are held
  * in 64-bit words; with W = 32 only the low 32 bits are used and produced. */
 void mpro_philox(int W, int rounds, const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+/* The block function on n counters (ctr and out: n x 4 words, row-major). */
+void mpro_philox_n(int W, int rounds, int n, const uint64_t* ctr, const uint64_t key[2],
+                   uint64_t* out);
 
 /* The two 32-bit random words of site (x, y) at the given sweep and tag (0 Metropolis, 1 init). */
 void mpro_site_words(const mpro_cfg* cfg, int x, int y, uint32_t sweep, int tag,
