@@ -197,7 +197,10 @@ mpr_status mpr_set_sweep_kernel(mpr_handle h, int kind);
  * w <- w exp(a - target), a = the sweep's accepted proposals / n_pred, w kept in [1e-3, 2 pi]; the
  * width then stays fixed while sampling (target = 0: fixed width). The width lives on the
  * device; both FP32 and FP64 function setups support it, the FP32 ones through sweep kernel
- * kind 0 only (mpr_get_info reports kind 0 while it is on). Synchronises the handle's stream.
+ * kind 0 only (mpr_get_info reports kind 0 while it is on). The setting and the adapted width
+ * stay across mpr_set_options and mpr_set_state (a checkpoint that must resume the same chain
+ * saves the width from mpr_get_proposal and sets it again with target 0 or its old target).
+ * Batched handles draw uniform proposals. Synchronises the handle's stream.
  * INVALID_ARG for width outside [0, 2 pi] or target outside [0, 1). */
 mpr_status mpr_set_proposal(mpr_handle h, double width, double target);
 /* Current half-width of the bounded proposal (0 when proposals are uniform); synchronises. */
