@@ -54,13 +54,13 @@ cudaError_t batch_occupancy(int store, int shape, int* blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k.persistent, 256, k.smem);
 }
 
-cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args_dev, cudaStream_t st,
-                         bool use_graph)
+cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args_dev,
+                         const PhiloxSched& keys, cudaStream_t st, bool use_graph)
 {
     const batch::Kernels kk = kernels_for(store, shape);
     const void* k = kk.persistent;
     if (!k) return cudaErrorInvalidValue;
-    void* params[] = {const_cast<batch::Args**>(&args_dev)};
+    void* params[] = {const_cast<batch::Args**>(&args_dev), const_cast<PhiloxSched*>(&keys)};
     if (!use_graph)
         return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(32, f32::kWarps), params, kk.smem, st);
     // the same launch as a one-node CUDA graph with a cooperative kernel node
@@ -88,7 +88,7 @@ cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args
 }
 
 cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::Args* args_dev,
-                              cudaGraphExec_t* out)
+                              const PhiloxSched& keys, cudaGraphExec_t* out)
 {
     const batch::Kernels kk = kernels_for(store, shape);
     const void* pass = kk.pass;
@@ -112,7 +112,8 @@ cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::
     const int red = 0, black = 1;
     cudaGraphNode_t n_red, n_black, n_fin;
     if (e == cudaSuccess) {
-        void* params[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&red)};
+        void* params[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&red),
+                          const_cast<PhiloxSched*>(&keys)};
         cudaKernelNodeParams kp{};
         kp.func = const_cast<void*>(pass);
         kp.gridDim = dim3(max_tiles);
@@ -121,7 +122,8 @@ cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::
         kp.kernelParams = params;
         e = cudaGraphAddKernelNode(&n_red, body, nullptr, 0, &kp);
         if (e == cudaSuccess) {
-            void* params_b[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&black)};
+            void* params_b[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&black),
+                                const_cast<PhiloxSched*>(&keys)};
             kp.kernelParams = params_b;
             e = cudaGraphAddKernelNode(&n_black, body, &n_red, 1, &kp);
         }

@@ -107,11 +107,13 @@ Kernels kernels_f64(int shape);
 }  // namespace batch
 
 cudaError_t batch_occupancy(int store, int shape, int* blocks_per_sm);
-cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args_dev, cudaStream_t st,
-                         bool use_graph);
+// keys: the batch's Philox round keys (philox_sched of its seed; only k[] is read), a kernel
+// parameter of every tile kernel.
+cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args_dev,
+                         const PhiloxSched& keys, cudaStream_t st, bool use_graph);
 // Graph mode: an executable graph whose device-side while loop runs red pass, black pass and the
 // finish kernel until no problem is active (or max_iters). max_tiles = blocks of a pass kernel.
 cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::Args* args_dev,
-                              cudaGraphExec_t* out);
+                              const PhiloxSched& keys, cudaGraphExec_t* out);
 
 }  // namespace mpr

@@ -269,6 +269,8 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.seed_hi = (uint32_t)(b->opt.seed >> 32);
     A.q = b->opt.q;
     A.qf = (float)b->opt.q;
+    // round keys of the batch's seed for the tile kernels' parameter (counter parts unused)
+    const PhiloxSched keys = philox_sched(0u, 0u, kTagMetropolis, 0u, A.seed_lo, A.seed_hi);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
@@ -283,12 +285,13 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
                 ge = nullptr;
             }
             if (!ge) {
-                BCU(batch_graph_build(b->prec.store, b->shape, b->ntiles, b->dArgs, &ge));
+                BCU(batch_graph_build(b->prec.store, b->shape, b->ntiles, b->dArgs, keys, &ge));
                 b->gexec_tiles[b->shape] = b->ntiles;
             }
             BCU(cudaGraphLaunch(ge, b->stream));
         } else {
-            BCU(batch_launch(b->prec.store, b->shape, grid, b->dArgs, b->stream, b->use_graph != 0));
+            BCU(batch_launch(b->prec.store, b->shape, grid, b->dArgs, keys, b->stream,
+                             b->use_graph != 0));
         }
         b->launches += 1;
     }

@@ -222,10 +222,12 @@ __device__ void bookkeeping(Prob& P, const Args& A, double raw)
 
 // Builds the sweep arguments of tile t (colour `colour`) and runs it. One function per variant,
 // not inlined, so every variant gets its own register allocation within the kernel's budget; the
-// arguments are a pointer and scalars, so nothing passes through local memory.
-template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
+// arguments are a pointer and scalars, so nothing passes through local memory. ks (SCHED): the
+// kernel parameter holding the batch's Philox round keys (one seed for every problem), so they
+// enter the rounds as constant operands; the counter-dependent half of round 1 is formed per tile.
+template <typename S, int R, int TJ, bool MEASURE, int SAMPLE, bool SCHED>
 __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour,
-                                          int tx, int ty)
+                                          int tx, int ty, const PhiloxSched* ks)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const Prob& P = A->prob[p];
@@ -254,8 +256,15 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
     a.invT = 0.0;        // the FP32 tile uses qf and invTf only
     a.qf = A->qf;
     a.invTf = __ldcg(&P.d.invTf);
+    if constexpr (SCHED) {
+        a.ph = *ks;
+        const uint64_t m = (uint64_t)0xCD9E8D57u * a.sweep;
+        a.ph.a = (uint32_t)(m >> 32) ^ a.seed_lo;
+        a.ph.b = (uint32_t)m;
+        a.ph.c = (((uint32_t)p << 8) | (kTagMetropolis << 1) | (uint32_t)colour) ^ a.seed_hi;
+    }
     void* eslot = MEASURE ? static_cast<char*>(A->epart) + (size_t)t * (A->energy_f32 ? 4 : 8) : nullptr;
-    sweep_tile<S, R, MEASURE, SAMPLE, false>(a, tx, ty,
+    sweep_tile<S, R, MEASURE, SAMPLE, SCHED>(a, tx, ty,
                                              *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
 }
 
@@ -263,16 +272,17 @@ template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
 __device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour, int tx,
                                      int ty)
 {
-    tile_body<S, R, TJ, MEASURE, SAMPLE>(A, t, p, colour, tx, ty);
+    tile_body<S, R, TJ, MEASURE, SAMPLE, false>(A, t, p, colour, tx, ty, nullptr);
 }
 
 // The variant of a tile of shape (R, TJ) for this pass: plain inlined, the others as calls.
 template <typename S, int R, int TJ>
 __device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, int p, int colour,
-                                             int tx, int ty, bool measure, bool sample)
+                                             int tx, int ty, bool measure, bool sample,
+                                             const PhiloxSched& ks)
 {
     if (!measure && !sample) {
-        tile_body<S, R, TJ, false, 0>(A, t, p, colour, tx, ty);
+        tile_body<S, R, TJ, false, 0, true>(A, t, p, colour, tx, ty, &ks);
     } else if (measure && !sample) {
         tile_fn<S, R, TJ, true, 0>(A, t, p, colour, tx, ty);
     } else if (!measure) {
@@ -288,7 +298,7 @@ __device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, 
 // variants are calls.
 template <typename S, int R, int TJ>
 __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p, int colour,
-                                        TileSmem<R, TJ>& sm)
+                                        TileSmem<R, TJ>& sm, const PhiloxSched& ks)
 {
     Prob& P = A->prob[p];
     const int ph = __ldcg(&P.d.phase);
@@ -303,11 +313,11 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p
     constexpr bool kTail = TJ == 128 && R % 2 == 0;
     if constexpr (kTail) {
         if (P.tail64 && tx == P.ntx - 1)
-            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample);
+            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
         else
-            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample);
+            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
     } else {
-        tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample);
+        tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
     }
     if (colour == 1) {
         __shared__ int s_last;
@@ -337,7 +347,8 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p
 // tile runs.
 template <typename S, int R, int TJ>
 __device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const int2* list, int n,
-                                            int colour, TileSmem<R, TJ>& sm, volatile int* s_k)
+                                            int colour, TileSmem<R, TJ>& sm, volatile int* s_k,
+                                            const PhiloxSched& ks)
 {
     if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
     __syncthreads();
@@ -346,7 +357,7 @@ __device__ __forceinline__ void colour_pass(const Args* __restrict__ A, const in
         __syncthreads();   // every thread has read s_k
         if (threadIdx.x == 0 && threadIdx.y == 0) *s_k = (int)atomicAdd(&A->ctl->work[colour], 1u);
         const int2 e = __ldcg(list + k);
-        do_tile<S, R, TJ>(A, e.x, e.y, colour, sm);
+        do_tile<S, R, TJ>(A, e.x, e.y, colour, sm, ks);
         __syncthreads();
         k = *s_k;
     }
@@ -383,7 +394,8 @@ __device__ void compact_list(const Args* __restrict__ A, const int2* src, int n,
 }
 
 template <typename S, int R, int TJ>
-__global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ A)
+__global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ A,
+                                                        const PhiloxSched ks)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     TileSmem<R, TJ>& sm = *reinterpret_cast<TileSmem<R, TJ>*>(dsm);
@@ -400,9 +412,9 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
     for (int it = 0; it < A->max_iters; ++it) {
         const int2* list = A->lists + (size_t)s_sel * A->ntiles;
         const int n = s_n;
-        colour_pass<S, R, TJ>(A, list, n, 0, sm, &s_k);
+        colour_pass<S, R, TJ>(A, list, n, 0, sm, &s_k, ks);
         if (!grid_barrier(ctl, expected, &s_err, &ctl->work[0])) return;
-        colour_pass<S, R, TJ>(A, list, n, 1, sm, &s_k);
+        colour_pass<S, R, TJ>(A, list, n, 1, sm, &s_k, ks);
         if (!grid_barrier(ctl, expected, &s_err, &ctl->work[1])) return;
         if (t0) {
             s_active = __ldcg(&ctl->n_active);
@@ -439,14 +451,15 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
 // Compiled for 4 resident blocks per SM: the inlined plain tile (most passes) fits 64 registers;
 // the rarer energy and sampling variants are calls that may spill.
 template <typename S, int R, int TJ>
-__global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A, int colour)
+__global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A, int colour,
+                                                       const PhiloxSched ks)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const Ctl* ctl = A->ctl;
     const int k = blockIdx.x;
     if (k >= __ldcg(&ctl->n_list)) return;
     const int2 e = __ldcg(A->lists + (size_t)__ldcg(&ctl->list_sel) * A->ntiles + k);
-    do_tile<S, R, TJ>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R, TJ>*>(dsm));
+    do_tile<S, R, TJ>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R, TJ>*>(dsm), ks);
 }
 
 
