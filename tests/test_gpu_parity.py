@@ -651,6 +651,86 @@ def test_full_size_sweep_sampled_sites(mpr, orc, L, setup):
         assert excused < 40, (c, excused)
 
 
+def test_maximum_lattice_size(mpr, orc):
+    # The largest lattice the ABI accepts (N < 2^31 sites: 65536 x 32767 = 2 147 418 112), HDS,
+    # inputs on the device: every element offset beyond 2^31 bytes (FP64 inputs, accumulators,
+    # state transfer) and the last rows and columns go through the same one-sweep check as the
+    # full-size test, with the sampled sites weighted toward the end of the arrays; frozen sites
+    # bit for bit.
+    import torch
+
+    Lx, Ly = 65536, 32767
+    dev = torch.device("cuda", 0)
+    # one row more is 2^31 sites: refused before the buffers are read
+    import ctypes
+
+    small = np.zeros(4)
+    hh = ctypes.c_void_p()
+    st = mpr.load().mpr_create(Lx, Ly + 1, small.ctypes.data_as(ctypes.c_void_p),
+                               small.ctypes.data_as(ctypes.c_void_p), ctypes.byref(hh))
+    assert st == mpr.MPR_ERR_INVALID_ARG and not hh.value
+    ys = torch.arange(Ly, device=dev, dtype=torch.float64)[:, None]
+    xs = torch.arange(Lx, device=dev, dtype=torch.float64)[None, :]
+    z = 50.0 + 10.0 * torch.sin(xs / 61.0) * torch.cos(ys / 47.0)
+    del xs, ys
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    mask = (torch.rand((Ly, Lx), generator=g, device=dev) >= 0.9).to(torch.uint8)
+    T, seed = 0.07, 7
+    h = mpr.mpr_create_dev(z, mask)
+    try:
+        mpr.mpr_set_options(h, "HDS", seed=seed)
+        state, sw0 = mpr.mpr_get_state(h)
+        mpr.mpr_set_temperature(h, T)
+        mpr.mpr_run(h, 1, 0)
+        got, sw = mpr.mpr_get_state(h)
+        info = mpr.mpr_get_info(h)
+    finally:
+        mpr.mpr_destroy(h)
+    del z
+    mask8 = mask.cpu().numpy()
+    del mask
+    torch.cuda.empty_cache()
+    assert sw == sw0 + 1 and info["n_sites"] == Lx * Ly
+    frozen = mask8 == 1
+    assert np.array_equal(got[frozen].view(np.uint64), state[frozen].view(np.uint64))
+    del frozen
+    o = _oracle(orc, Lx, Ly, seed, "HDS")
+    tol = 1e-4 + 2 * _ulp_store("HDS")
+    rng = np.random.default_rng(11)
+    # sampled rows: uniform, plus the last 16 rows; columns uniform plus the last 16
+    rows = np.concatenate([rng.integers(0, Ly, 300), Ly - 1 - rng.integers(0, 16, 300)])
+    cols = np.concatenate([rng.integers(0, Lx, 300), Lx - 1 - rng.integers(0, 16, 300)])
+    rng.shuffle(cols)
+    checked = {0: 0, 1: 0}
+    for c in (0, 1):
+        bad = excused = 0
+        for y, x in zip(rows, cols):
+            y, x = int(y), int(x)
+            if (x + y) % 2 != c:   # move to the neighbouring column: a site of colour c
+                x = x - 1 if x > 0 else x + 1
+            if mask8[y, x]:
+                continue
+            nbr = [(yy, xx) for yy, xx in ((y, x - 1), (y, x + 1), (y - 1, x), (y + 1, x))
+                   if 0 <= yy < Ly and 0 <= xx < Lx]
+            saved = [state[yy, xx] for yy, xx in nbr]
+            if c == 1:   # black: the GPU's red neighbours as inputs
+                for yy, xx in nbr:
+                    state[yy, xx] = got[yy, xx]
+            f, mm, om = o.update_site(state, mask8, x, y, T, sw0)
+            for (yy, xx), v in zip(nbr, saved):
+                state[yy, xx] = v
+            checked[c] += 1
+            if mm < 1e-4 or om < 1e-4:
+                excused += 1
+                continue
+            if abs(got[y, x] - _round_store(np.array([f]), "HDS")[0]) > tol:
+                bad += 1
+        assert bad == 0, (c, bad)
+        assert excused < 20, (c, excused)
+    assert min(checked.values()) > 400, checked
+
+
 # --- energy-slope equilibration ----------------------------------------------------------------
 
 def test_run_auto_matches_oracle_ddd(mpr, orc):
