@@ -306,9 +306,14 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, uint32_t* __rest
 // Width of the bounded Metropolis proposals after one sweep: w <- w exp(a - target), with a the
 // sweep's acceptance fraction over the n_pred prediction sites, kept in [1e-3, 2 pi]; the
 // counter restarts at 0 for the next sweep.
+// Launched as a programmatic dependent launch between two sweeps: it waits for the black pass it
+// follows, then lets the next red pass be scheduled at once (that pass still waits for this
+// kernel's completion before it reads the width).
 __global__ void adapt_width_kernel(double* __restrict__ width, unsigned long long* __restrict__ count,
                                    long long n_pred, double target)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     const double acc = n_pred > 0 ? (double)*count / (double)n_pred : target;
     *width = fmin(fmax(*width * exp(acc - target), 1e-3), 6.283185307179586);
     *count = 0ull;
@@ -438,8 +443,16 @@ cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* 
 cudaError_t launch_adapt_width(double* width, unsigned long long* count, long long n_pred,
                                double target, cudaStream_t st)
 {
-    adapt_width_kernel<<<1, 1, 0, st>>>(width, count, n_pred, target);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(1);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, adapt_width_kernel, width, count, n_pred, target);
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed, cudaStream_t st)

@@ -20,10 +20,12 @@ constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 
 // Compiled for 4 resident blocks per SM (64 registers: no spills with 16-bit spins, a few bytes
 // with FP32 spins in the energy and sampling variants); 2 for FP64 spins, whose values take
-// twice the registers and would spill at 3 or 4. Bounded proposals keep the old angle and the
-// half-width live across the move: 3 blocks per SM, without spills.
+// twice the registers and would spill at 3 or 4. Bounded proposals keep the half-width and the
+// acceptance count live across the moves: their plain pass with 16-bit spins still fits 4 blocks
+// per SM; the others run at 3, without spills.
 template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : (PROP ? 3 : 4))
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
+                                       : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
     sweep_f32_kernel(const SweepArgs a)
 {
     static_assert(R % 2 == 0, "the 64-column tail tile has R / 2 rows per thread");

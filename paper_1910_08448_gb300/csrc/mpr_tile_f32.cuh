@@ -406,12 +406,22 @@ __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, i
     }
 }
 
-// Adds the block's accepted bounded proposals to *counter: one atomic per warp.
+// Adds the block's accepted bounded proposals to *counter: warp sums, then one atomic per block
+// (every block of a pass adds to the same word, so fewer atomics means less serialisation at L2).
+// Called by every thread of the block.
 __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* counter)
 {
+    __shared__ int s_acc[kWarps];
 #pragma unroll
     for (int off = 16; off; off >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, off);
-    if (threadIdx.x == 0 && n_acc) atomicAdd(counter, (unsigned long long)n_acc);
+    if (threadIdx.x == 0) s_acc[threadIdx.y] = n_acc;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += s_acc[w];
+        if (t) atomicAdd(counter, (unsigned long long)t);
+    }
 }
 
 // One tile (tile column tx, tile row ty) of colour a.colour, staged from global memory. With
