@@ -37,8 +37,9 @@ struct Prob {
     double Nb;                  // bonds
     double e_s;                 // sample energy
     unsigned tiles_done;        // black tiles finished in this sweep (arrival counter)
-    int tail64;                 // 128-column tiles: the last tile column is 64 wide (it holds
-                                // at most 64 columns), run with the 64-column tile code
+    int tail;                   // 128-column tiles: 0, or the width (64 or 32) of the narrower
+                                // tile code that runs the last tile column (it holds at most
+                                // that many columns)
     Dyn d;
 };
 

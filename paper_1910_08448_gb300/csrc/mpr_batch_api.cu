@@ -157,8 +157,10 @@ mpr_status build_tiles(mpr_batch_ctx* b, int shape)
     if (b->tiled_shape == shape) return MPR_OK;
     const int TY = batch::shape_rows(shape), TJ = batch::shape_cols(shape);
     // 128-column shapes with an even row count per thread run a last tile column of at most 64
-    // columns as a 64-column tile (see do_tile)
+    // columns as a 64-column tile, and with a row count per thread divisible by 4 one of at most
+    // 32 columns as a 32-column tile (see do_tile)
     const bool tail = TJ == 128 && batch::kShape[shape].rpt % 2 == 0;
+    const bool tail32 = TJ == 128 && batch::kShape[shape].rpt % 4 == 0;
     b->tile_prob.clear();
     std::vector<long long> cost;
     for (int i = 0; i < b->n; ++i) {
@@ -167,14 +169,14 @@ mpr_status build_tiles(mpr_batch_ctx* b, int shape)
         p.nty = (p.Ly + TY - 1) / TY;
         p.ntiles = p.ntx * p.nty;
         const int rem = p.Lxh - (p.ntx - 1) * TJ;   // columns of the last tile column
-        p.tail64 = tail && rem <= 64 ? 1 : 0;
+        p.tail = tail32 && rem <= 32 ? 32 : (tail && rem <= 64 ? 64 : 0);
         p.tile_base = (int)b->tile_prob.size();
         for (int t = 0; t < p.ntiles; ++t) {
             b->tile_prob.push_back(i);
             const int tx = t % p.ntx, ty = t / p.ntx;
             const long long w = std::min(TJ, p.Lxh - tx * TJ), h = std::min(TY, p.Ly - ty * TY);
-            // cost of a tile: the lattice entries its block sweeps (a 64-column tail tile: 64)
-            const long long wt = (p.tail64 && tx == p.ntx - 1) ? std::min(64LL, w) : w;
+            // cost of a tile: the lattice entries its block sweeps (a tail tile: its width)
+            const long long wt = (p.tail && tx == p.ntx - 1) ? std::min((long long)p.tail, w) : w;
             cost.push_back(wt * h);
         }
     }

@@ -309,10 +309,21 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p
     const int tx = i % P.ntx, ty = i / P.ntx;
     // 128-column tiles with an even row count per thread: a problem whose last tile column holds
     // at most 64 columns runs that column with the 64-column code of the same height (tile column
-    // 2 tx in 64-column units), wasting half as much of the tile
+    // 2 tx in 64-column units), wasting half as much of the tile; with a row count per thread
+    // divisible by 4, one of at most 32 columns runs with the 32-column code (tile column 4 tx)
     constexpr bool kTail = TJ == 128 && R % 2 == 0;
-    if constexpr (kTail) {
-        if (P.tail64 && tx == P.ntx - 1)
+    constexpr bool kTail32 = TJ == 128 && R % 4 == 0;
+    const bool last = tx == P.ntx - 1;
+    if constexpr (kTail32) {
+        if (last && P.tail == 32) {
+            tile_variant<S, R / 4, 32>(A, t, p, colour, 4 * tx, ty, measure, sample, ks);
+        } else if (last && P.tail == 64) {
+            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
+        } else {
+            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
+        }
+    } else if constexpr (kTail) {
+        if (last && P.tail == 64)
             tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
         else
             tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
                                        : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
     sweep_f32_kernel(const SweepArgs a)
 {
-    static_assert(R % 2 == 0, "the 64-column tail tile has R / 2 rows per thread");
+    static_assert(R % 4 == 0, "the 64- and 32-column tail tiles have R / 2 and R / 4 rows per thread");
     __shared__ __align__(16) TileSmem<R> sm;
     // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
     const int b = blockIdx.x;
@@ -37,10 +37,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    // a last tile column of at most 64 columns runs as a 64-column tile of the same height (tile
-    // column 2 tx in 64-column units), as the batched kernels do: the energy partials, and so the
-    // energies, stay bit-identical between the two paths
-    if (tx == ntx - 1 && a.Lxh - tx * kTJ <= 64)
+    // a last tile column of at most 32 (64) columns runs as a 32- (64-) column tile of the same
+    // height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the batched kernels
+    // do: the energy partials, and so the energies, stay bit-identical between the two paths
+    const int rem = a.Lxh - tx * kTJ;
+    if (tx == ntx - 1 && rem <= 32)
+        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32>(
+            a, 4 * tx, ty, *reinterpret_cast<TileSmem<R / 4, 32>*>(&sm), eslot);
+    else if (tx == ntx - 1 && rem <= 64)
         sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64>(
             a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
     else

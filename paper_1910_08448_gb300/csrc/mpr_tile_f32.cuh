@@ -23,7 +23,7 @@ constexpr int kWarps = 8;    // 256 threads, blockDim = (32, 8)
 
 // Lanes of a warp per tile row (TJ / 4) and tile rows per warp step.
 template <int TJ> struct Lanes {
-    static_assert(TJ == 128 || TJ == 64, "tile width");
+    static_assert(TJ == 128 || TJ == 64 || TJ == 32, "tile width");
     static constexpr int kPerRow = TJ / 4;
     static constexpr int kRows = 32 / kPerRow;
 };
