@@ -111,6 +111,11 @@ mpr_status mpr_create(int Lx, int Ly, const double* values, const unsigned char*
 mpr_status mpr_create_dev(int Lx, int Ly, const double* values_dev, const unsigned char* mask_dev,
                           void* stream, mpr_handle* out);
 void mpr_destroy(mpr_handle h);
+/* Device memory of handles comes from one stream-ordered pool per device that the library owns;
+ * up to 8 GiB of freed memory stays cached there for the next handles (no driver call, no
+ * device-wide synchronisation at creation or destruction). This returns every cached byte to
+ * the driver (handles alive keep theirs). */
+mpr_status mpr_trim_memory(void);
 
 /* Replaces the options and restarts the chain: the spins are re-initialised, the sweep counter,
  * the samples and the temperature are cleared. */

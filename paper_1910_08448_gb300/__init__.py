@@ -83,6 +83,7 @@ def load():
             "mpr_create": ([i, i, vp, vp, P(H)], i),
             "mpr_create_dev": ([i, i, vp, vp, vp, P(H)], i),
             "mpr_destroy": ([H], None),
+            "mpr_trim_memory": ([], i),
             "mpr_set_options": ([H, P(mpr_options)], i),
             "mpr_get_options": ([H, P(mpr_options)], i),
             "mpr_set_stream": ([H, vp], i),
@@ -132,7 +133,8 @@ def load():
 
 def exported_symbols():
     """Names the binding expects the library to export (every function of include/mpr.h)."""
-    return ["mpr_create", "mpr_create_dev", "mpr_destroy", "mpr_set_options", "mpr_get_options",
+    return ["mpr_create", "mpr_create_dev", "mpr_destroy", "mpr_trim_memory", "mpr_set_options",
+            "mpr_get_options",
             "mpr_set_stream", "mpr_set_tuning", "mpr_tune_temperature", "mpr_set_temperature",
             "mpr_tune_heating", "mpr_energy_curve", "mpr_tune_from_curve",
             "mpr_run", "mpr_run_auto", "mpr_predict", "mpr_predict_dev", "mpr_energy", "mpr_get_info",
@@ -202,6 +204,11 @@ def mpr_destroy(h):
     if h is not None and h.value:
         load().mpr_destroy(h)
         h.value = None
+
+
+def mpr_trim_memory():
+    """Returns the device memory cached by the library's pool to the driver."""
+    _check(load().mpr_trim_memory())
 
 
 def make_options(setup: str = "SDS", seed: int = 0, q: float = 0.5, acc: str = "f64") -> mpr_options:

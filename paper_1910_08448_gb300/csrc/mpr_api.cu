@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -147,27 +148,63 @@ inline unsigned long long* prop_count(mpr_ctx* h)
 
 namespace {
 
+// Device memory of the handles: one stream-ordered pool per device, owned by the library. Freed
+// blocks stay in the pool up to kPoolKeepBytes (returned to the driver beyond that at the next
+// synchronisation), so a handle created after another one of similar size allocates without a
+// driver call or a device-wide synchronisation; mpr_trim_memory returns everything.
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t handle_pool(int device, cudaMemPool_t* out)
+{
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = kPoolKeepBytes;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[device] = pool;
+    }
+    *out = g_pool[device];
+    return cudaSuccess;
+}
+
 template <typename T>
 mpr_status dalloc(mpr_ctx* h, T** p, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = handle_pool(h->device, &pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q, bytes, pool, h->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? MPR_ERR_OOM : MPR_ERR_CUDA,
-                    "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+                    "device allocation (%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     *p = static_cast<T*>(q);
     h->bytes += bytes;
     return MPR_OK;
 }
 
+// Stream-ordered: the block returns to the pool after the work queued before it on the stream.
 template <typename T>
 void dfree(mpr_ctx* h, T** p, size_t bytes)
 {
     if (*p) {
-        cudaFree(*p);
+        cudaFreeAsync(*p, h->stream);
         h->bytes -= bytes ? bytes : 16;
     }
     *p = nullptr;
@@ -545,7 +582,19 @@ void mpr_destroy(mpr_handle h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     free_all(h);
+    cudaStreamSynchronize(h->stream);   // the frees are stream-ordered: complete them here
     delete h;
+}
+
+mpr_status mpr_trim_memory(void)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (cudaMemPool_t pool : g_pool) {
+        if (!pool) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(pool, 0);
+        if (e != cudaSuccess) return fail(MPR_ERR_CUDA, "cudaMemPoolTrimTo: %s", cudaGetErrorString(e));
+    }
+    return MPR_OK;
 }
 
 mpr_status mpr_set_options(mpr_handle h, const mpr_options* opt)

@@ -410,6 +410,27 @@ def test_problem_class_equals_the_c_calls(mpr):
         assert np.array_equal(out.cpu().numpy(), ref)
 
 
+def test_handles_reuse_pooled_memory(mpr):
+    # handles of one size in a row draw their device memory from the library's pool: every run
+    # starts from its own initialisation (nothing leaks from the previous handle's blocks), and
+    # trimming the pool leaves later handles working
+    pr = mpr_inputs.make_problem(600, 300, 0.9, field_seed=23, mask_seed=24)
+    out = []
+    for k in range(4):
+        h = mpr.mpr_create(pr.z, pr.mask)
+        try:
+            mpr.mpr_set_options(h, "HDS", seed=3)
+            mpr.mpr_set_temperature(h, 0.2)
+            mpr.mpr_run(h, 20, 5)
+            out.append((mpr.mpr_get_state(h)[0], mpr.mpr_predict(h)))
+        finally:
+            mpr.mpr_destroy(h)
+        if k == 1:
+            mpr.mpr_trim_memory()
+    for st, zh in out[1:]:
+        assert np.array_equal(st, out[0][0]) and np.array_equal(zh, out[0][1])
+
+
 # --- checkpoint / resume and other q -------------------------------------------------------
 
 @pytest.mark.parametrize("setup", ["DDD", "SDS", "HDS"])
