@@ -30,27 +30,40 @@ template <int TJ> struct Lanes {
 
 // Twice atan2(y, x) modulo 2*pi, in FP32, as an angle in [-pi, pi] (the over-relaxation needs the
 // doubled angle only modulo 2*pi). Reduce to a = min(|x|,|y|)/max(|x|,|y|) in [0, 1] and evaluate
-// 2 atan(a) = a*P(a^2); P is a degree-7 polynomial in a^2 fitted for this library by Lawson's
-// iteratively reweighted least squares (a minimax method) to atan on [0, 1], max error 3.8e-8
-// rad, here with every coefficient doubled (exact: Horner's rounding commutes with the factor 2).
+// 2 atan(a) = a*P(a^2); P is a polynomial in a^2 fitted for this library by Lawson's iteratively
+// reweighted least squares (a minimax method) to atan on [0, 1], here with every coefficient
+// doubled (exact: Horner's rounding commutes with the factor 2). SHORT (16-bit spin storage): 6
+// coefficients, max error 1.7e-6 rad (3.5e-6 on the doubled angle in FP32, three orders below the
+// storage's 2^-8 rad spacing near 2 pi); otherwise 8 coefficients, max error 3.8e-8 rad.
 // In the first quadrant the doubled angle is 2t (|y| <= |x|) or pi - 2t; reflecting into the other
 // quadrants maps it to its negative modulo 2 pi (x < 0: 2(pi - t1) = -2 t1; y < 0: -2 t1), so the
 // sign of the result is the sign of x*y, applied by flipping the sign bit. The quotient uses the
 // approximate FP32 division; x = y = 0 gives NaN.
+template <bool SHORT>
 __device__ __forceinline__ float atan2_doubled(float y, float x)
 {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
     const float a = __fdividef(mn, mx);
     const float s = a * a;
-    float p = -0.008109131827950478f;
-    p = fmaf(p, s, 0.04372590780258179f);
-    p = fmaf(p, s, -0.1118246391415596f);
-    p = fmaf(p, s, 0.1928439438343048f);
-    p = fmaf(p, s, -0.2781725823879242f);
-    p = fmaf(p, s, 0.3989313244819641f);
-    p = fmaf(p, s, -0.6665971875190735f);
-    p = fmaf(p, s, 1.999998688697815f);
+    float p;
+    if constexpr (SHORT) {
+        p = -0.023438263684511185f;
+        p = fmaf(p, s, 0.10529468208551407f);
+        p = fmaf(p, s, -0.23285295069217682f);
+        p = fmaf(p, s, 0.38708075881004333f);
+        p = fmaf(p, s, -0.6652456521987915f);
+        p = fmaf(p, s, 1.9999544620513916f);
+    } else {
+        p = -0.008109131827950478f;
+        p = fmaf(p, s, 0.04372590780258179f);
+        p = fmaf(p, s, -0.1118246391415596f);
+        p = fmaf(p, s, 0.1928439438343048f);
+        p = fmaf(p, s, -0.2781725823879242f);
+        p = fmaf(p, s, 0.3989313244819641f);
+        p = fmaf(p, s, -0.6665971875190735f);
+        p = fmaf(p, s, 1.999998688697815f);
+    }
     float t2 = a * p;
     t2 = (ay > ax) ? 3.14159265358979324f - t2 : t2;
     const uint32_t sgn = (__float_as_uint(x) ^ __float_as_uint(y)) & 0x80000000u;
@@ -294,7 +307,7 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
             // h = 0 gives NaN in atan2_doubled, every comparison below is false and the angle
             // stays, as the move requires.
-            float r = atan2_doubled(hyk, hxk) - q * f1;   // in [-pi - 2 pi q, pi]
+            float r = atan2_doubled<sizeof(S) == 2>(hyk, hxk) - q * f1;   // in [-pi - 2 pi q, pi]
             // r < 0 ? r + 2 pi : r, twice, on the FMA pipe: the saturated product is 1 for every
             // negative normal r and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the
             // rounding of a plain add. (A nonzero r is never subnormal: its two terms are 0 or at
