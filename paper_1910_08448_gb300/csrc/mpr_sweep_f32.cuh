@@ -23,6 +23,26 @@ constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 // twice the registers and would spill at 3 or 4. Bounded proposals keep the half-width and the
 // acceptance count live across the moves: their plain pass with 16-bit spins still fits 4 blocks
 // per SM; the others run at 3, without spills.
+// The tile of block b: a last tile column of at most 32 (64) columns runs as a 32- (64-) column
+// tile of the same height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the
+// batched kernels do: the energy partials, and so the energies, stay bit-identical between the
+// two paths.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, bool W1>
+__device__ __forceinline__ void block_tile(const SweepArgs& a, int b, TileSmem<R>& sm, void* eslot)
+{
+    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    const int tx = b % ntx, ty = b / ntx;
+    const int rem = a.Lxh - tx * kTJ;
+    if (tx == ntx - 1 && rem <= 32)
+        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32, W1>(
+            a, 4 * tx, ty, *reinterpret_cast<TileSmem<R / 4, 32>*>(&sm), eslot);
+    else if (tx == ntx - 1 && rem <= 64)
+        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64, W1>(
+            a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
+    else
+        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, W1>(a, tx, ty, sm, eslot);
+}
+
 template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
                                        : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
@@ -32,23 +52,19 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     __shared__ __align__(16) TileSmem<R> sm;
     // one tile per block, tiles row-major over a 1-D grid (no limit on the number of tile rows)
     const int b = blockIdx.x;
-    const int ntx = (a.Lxh + kTJ - 1) / kTJ;
-    const int tx = b % ntx, ty = b / ntx;
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    // a last tile column of at most 32 (64) columns runs as a 32- (64-) column tile of the same
-    // height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the batched kernels
-    // do: the energy partials, and so the energies, stay bit-identical between the two paths
-    const int rem = a.Lxh - tx * kTJ;
-    if (tx == ntx - 1 && rem <= 32)
-        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32>(
-            a, 4 * tx, ty, *reinterpret_cast<TileSmem<R / 4, 32>*>(&sm), eslot);
-    else if (tx == ntx - 1 && rem <= 64)
-        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64>(
-            a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
-    else
-        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP>(a, tx, ty, sm, eslot);
+    // the plain pass (most passes) with 16-bit spins has a copy for q <= 1/2 (the default) with
+    // one angle wrap; the branch is uniform over the grid (with FP32 spins the second copy would
+    // spill registers)
+    if constexpr (!MEASURE && SAMPLE == 0 && sizeof(S) == 2) {
+        if (a.qf <= 0.5f) {
+            block_tile<S, R, MEASURE, SAMPLE, PROP, true>(a, b, sm, eslot);
+            return;
+        }
+    }
+    block_tile<S, R, MEASURE, SAMPLE, PROP, false>(a, b, sm, eslot);
 }
 
 // Launched as a programmatic dependent launch: while the previous pass's last blocks finish, this

@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(256, 3)
             const int ly = warp * R + row_of<R>(i, a.colour);
             const int y = y0 + ly;
             if (y < a.Ly)
-                update_row_i<S, R, false, 0, true, false>(i, a, y, ly, jb, lj, mine[i], bits[i], sm.t,
-                                                          e_d, e_f, 0.0f, n_acc);
+                update_row_i<S, R, false, 0, true, false, false>(i, a, y, ly, jb, lj, mine[i],
+                                                                 bits[i], sm.t, e_d, e_f, 0.0f,
+                                                                 n_acc);
         }
         if (leader && tn < ntiles) await(it + 1);
         __syncthreads();   // the unit vectors' readers are done; sm.ok is current

@@ -219,7 +219,9 @@ template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, fl
 // (a kernel parameter) instead of the seed. OPAR: the row's column offset o = (y + colour) & 1
 // when the caller knows it at compile time (0 or 1), else -1. PROP: bounded proposals
 // f + pw (2u - 1), rejected outside [0, 2 pi); n_acc counts the accepted ones of updated sites.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, int TJ>
+// W1: the caller knows q <= 1/2, so the reflected angle needs one 2 pi wrap, not two.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, bool W1,
+          int TJ>
 __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
                                            Pack4<S>& pk, uint32_t bits, const TileSmem<R, TJ>& sm,
                                            double& e_d, float& e_f, float pw, int& n_acc)
@@ -312,8 +314,10 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             // negative normal r and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the
             // rounding of a plain add. (A nonzero r is never subnormal: its two terms are 0 or at
             // least ~1e-8 in magnitude.)
+            // (with q <= 1/2, r >= -2 pi and the first wrap already lands in [0, 2 pi); the second
+            // would add 0, so W1 drops it without changing a bit)
             r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
-            r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
+            if constexpr (!W1) r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
             const float fn = r <= width ? r * inv_q : f1;
             if constexpr (sizeof(S) == 2) {
                 // 16-bit storage: the pair's two results rounded by one conversion and merged into
@@ -400,7 +404,7 @@ template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R
 
 // update_row of the i-th row in the order row_of(), with o fixed at compile time for even R (the
 // branch on i & 1 disappears when the caller's loop over i is unrolled).
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, int TJ>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, bool W1, int TJ>
 __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
                                              int lj, Pack4<S>& pk, uint32_t bits,
                                              const TileSmem<R, TJ>& sm, double& e_d, float& e_f,
@@ -408,13 +412,13 @@ __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, i
 {
     if constexpr (R % 2 == 0) {
         if (i & 1)
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d,
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d,
                                                               e_f, pw, n_acc);
         else
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d,
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d,
                                                               e_f, pw, n_acc);
     } else {
-        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f,
+        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f,
                                                            pw, n_acc);
     }
 }
@@ -447,8 +451,9 @@ __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* co
 // Everything the previous pass may write (the other colour, accumulators, energy partials) is
 // touched only after the wait.
 // PROP: bounded proposals of half-width *a.width; accepted ones counted into *a.accepted.
+// W1: the caller has checked q <= 1/2 (one 2 pi wrap of the reflected angle suffices).
 template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false,
-          bool PROP = false, int TJ = kTJ>
+          bool PROP = false, int TJ = kTJ, bool W1 = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
@@ -498,7 +503,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const int ly = row0 + row_of<R>(i, c);
         const int y = y0 + ly;
         if (y < a.Ly)
-            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP>(i, a, y, ly, jb, lj, mine[i], bits[i],
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, W1>(i, a, y, ly, jb, lj, mine[i], bits[i],
                                                              sm, e_d, e_f, pw, n_acc);
     }
     if (PROP && a.accepted) count_accepted(n_acc, a.accepted);
