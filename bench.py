@@ -188,17 +188,19 @@ def sweep_kernel_id(kernel: str = "mpr::sweep_f32_kernel") -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel_id: str, kernel: str, workload: str):
+def stored_counters(kernel_id: str, kernel: str, workload: str):
+    """ncu counters of this kernel version on this workload (profiles/dram_traffic.json), or {}:
+    DRAM bytes per launch and the share of issue slots the kernel kept busy."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
-        return None
+        return {}
     e = d.get(workload)
     if not e or e.get("kernel_id") != kernel_id or e.get("kernel") != kernel:
-        return None
-    return e.get("bytes_per_launch")
+        return {}
+    return e
 
 
 # kernel that ran the plain passes, by mpr_info.sweep_kernel
@@ -321,7 +323,8 @@ def run_mine(args, dist: Dist):
     kname = SWEEP_KERNELS[infos[-1]["sweep_kernel"]]
     kid = sweep_kernel_id(kname)
     workload = f"L{L}_p{p}_{args.setup}" + ("_bounded" if proposal else "")
-    traffic = stored_traffic(kid, kname, workload)
+    counters = stored_counters(kid, kname, workload)
+    traffic = counters.get("bytes_per_launch")
     if t_hbm >= t_mufu:
         roof = {"bound": "hbm", "achieved": bytes_launch / t_launch / 1e9, "peak": hbm_gbs,
                 "unit": "GB/s"}
@@ -329,7 +332,11 @@ def run_mine(args, dist: Dist):
         roof = {"bound": "alu", "achieved": mufu_launch / t_launch / 1e9,
                 "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU, sin-equivalent)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof.update({"traffic": traffic, "peak_source": src if roof["bound"] == "hbm" else mufu_src,
+    roof.update({"traffic": traffic,
+                 # what limits this kernel: instruction issue (ncu smsp__issue_active, same kernel
+                 # version), next to the MUFU and HBM fractions
+                 "issue_active_ncu": counters.get("issue_active"),
+                 "peak_source": src if roof["bound"] == "hbm" else mufu_src,
                  "kernel": kname,
                  "launch_us": t_launch * 1e6, "algorithmic_bytes_per_launch": bytes_launch,
                  "algorithmic_mufu_per_launch": mufu_launch, "kernel_id": kid,
