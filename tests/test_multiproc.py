@@ -62,3 +62,8 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the oracle ran on the host's cores as independent replicas, with its one-thread rate beside
+    cb = d["cpu_baseline"]
+    assert cb["cores"] >= 1 and cb["value"] == d["value"]
+    if cb["cores"] > 1:
+        assert cb["single_thread"]["value"] > 0 and "processes" in cb["sample"]
