@@ -13,8 +13,10 @@
  *   specific energy e = <H>/L^2 ....................................... Sec. 2
  *   counter-based random numbers: Philox-4x32-10 ...................... Salmon et al., SC'11
  * Points on which the paper is silent (the mapping formula, open boundaries, the Metropolis
- * proposal, the over-relaxation reflection for q < 1, the tuning procedure) follow the readings
- * recorded in the design notes; each is restated at the function that uses it.
+ * proposal, the over-relaxation reflection for q < 1, the tuning procedure; and the options built
+ * on them: energy-slope equilibration, bounded proposals with an adapted width, tuning by heating
+ * and by the unconditional energy curve) follow the readings recorded in the design notes; each
+ * is restated at the function that uses it.
  */
 #include "mpr_oracle.h"
 
