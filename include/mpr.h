@@ -20,8 +20,8 @@
  *   - "host" pointers are ordinary CPU memory (pinned memory makes the copies faster); "dev"
  *     pointers are device memory of the current CUDA device, e.g. from torch. The library copies
  *     inputs; the caller keeps ownership of every pointer it passes.
- *   - The library allocates the device memory of a handle with cudaMalloc at creation and frees
- *     it in mpr_destroy.
+ *   - The library allocates the device memory of a handle at creation (from its stream-ordered
+ *     pool, see mpr_trim_memory; batches with cudaMalloc) and frees it in mpr_destroy.
  */
 #ifndef MPR_H
 #define MPR_H
@@ -110,6 +110,8 @@ mpr_status mpr_create(int Lx, int Ly, const double* values, const unsigned char*
  * which becomes the handle's stream. */
 mpr_status mpr_create_dev(int Lx, int Ly, const double* values_dev, const unsigned char* mask_dev,
                           void* stream, mpr_handle* out);
+/* Waits for the handle's queued work, then releases its device and pinned host memory (to the
+ * pool). NULL is ignored. */
 void mpr_destroy(mpr_handle h);
 /* Device memory of handles comes from one stream-ordered pool per device that the library owns;
  * up to 8 GiB of freed memory stays cached there for the next handles (no driver call, no
@@ -121,7 +123,10 @@ mpr_status mpr_trim_memory(void);
  * the samples and the temperature are cleared. */
 mpr_status mpr_set_options(mpr_handle h, const mpr_options* opt);
 mpr_status mpr_get_options(mpr_handle h, mpr_options* opt);
+/* Waits for the work queued on the old stream, then orders all later work on `stream`. */
 mpr_status mpr_set_stream(mpr_handle h, void* stream);
+/* INVALID_ARG for n_eq < 0, n_meas < 1, T_lo <= 0, T_hi <= T_lo, rel_tol < 0, ratio_tol <= 1 or
+ * max_probes outside [2, 64]. */
 mpr_status mpr_set_tuning(mpr_handle h, const mpr_tuning* t);
 
 /* Runs the tuning from the current state (the chain continues through the probes) and sets the
