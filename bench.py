@@ -256,7 +256,18 @@ def run_mine(args, dist: Dist):
     seed = 7 + dist.rank
     proposal = tuple(float(v) for v in args.proposal.split(",")) if args.proposal else None
 
-    def step_device(profile=False):
+    # phase boundaries of a job: CUDA events on the handle's stream (the legacy default stream,
+    # torch's current stream here), so tuning, equilibration and sampling are reported apart
+    PHASES = ("setup", "tune", "equil", "sample", "predict")
+
+    def mark(marks):
+        if marks is not None:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record()
+            marks.append(e)
+
+    def step_device(profile=False, marks=None):
+        mark(marks)
         h = mpr.mpr_create_dev(zt, mt)
         try:
             mpr.mpr_set_options(h, args.setup, seed=seed, acc=args.acc)
@@ -267,12 +278,18 @@ def run_mine(args, dist: Dist):
             mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
             if profile:
                 mpr.mpr_set_profiling(h, True)
+            mark(marks)
             T, _ = mpr.mpr_tune_temperature(h)
-            mpr.mpr_run(h, args.equil, args.samples)
+            mark(marks)
+            mpr.mpr_run(h, args.equil, 0)      # the same chain as one mpr_run(equil, samples)
+            mark(marks)
+            mpr.mpr_run(h, 0, args.samples)
+            mark(marks)
             mpr.mpr_predict_dev(h, out)
             info = mpr.mpr_get_info(h)
         finally:
             mpr.mpr_destroy(h)
+        mark(marks)
         return info
 
     for _ in range(args.warmup):
@@ -283,6 +300,7 @@ def run_mine(args, dist: Dist):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     infos = []
+    marks = [[] for _ in range(args.steps)]
     dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dist.local) as clk:
@@ -290,7 +308,7 @@ def run_mine(args, dist: Dist):
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record()
-            infos.append(step_device(profile=True))
+            infos.append(step_device(profile=True, marks=marks[k]))
             ev[k][1].record()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -302,6 +320,8 @@ def run_mine(args, dist: Dist):
     updates = dist.sum(updates_local)
     value = updates / (ms / 1e3)
     launches = int(sum(i["kernel_launches"] for i in infos))
+    phases_ms = {name: sum(m[i].elapsed_time(m[i + 1]) for m in marks) / args.steps
+                 for i, name in enumerate(PHASES)}
 
     # ---- dominant kernel: sweep half-pass, device time from CUDA events inside the steps ----
     sweep_ms = sum(i["prof_sweep_ms"] for i in infos)
@@ -416,6 +436,7 @@ def run_mine(args, dist: Dist):
         "ddd": ddd, "e2e": e2e, "clocks": clk.summary(), "accuracy": acc_rep,
         "wall_s": t_wall, "site_updates_per_step": updates_local / args.steps,
         "sweeps_per_step": infos[-1]["sweep"], "n_pred": infos[-1]["n_pred"], "problem": pr,
+        "phases_ms": phases_ms,
     }
 
 
@@ -695,6 +716,9 @@ def main():
             "fp64_gpu": res["ddd"], "accuracy": res["accuracy"],
             "site_updates_per_step": res["site_updates_per_step"],
             "sweeps_per_step": res["sweeps_per_step"], "wall_s_timed": res["wall_s"],
+            # device time per job by phase (CUDA events): set-up, tuning, equilibration, sampling,
+            # prediction and release
+            "phases_ms": res["phases_ms"],
         }
         print(json.dumps(line), flush=True)
     dist.close()
