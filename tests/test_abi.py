@@ -76,3 +76,16 @@ def test_host_validation_before_device_work(lib):
     assert lib.mpr_philox4x32_10_dev(None, None, -1, 0, None) == mpr.MPR_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         mpr.make_options("XYZ")
+    # the options of the hot path refuse a missing handle or bad arguments before any CUDA call
+    d = ctypes.c_double()
+    T = np.array([0.1, 0.2])
+    assert lib.mpr_set_proposal(None, 1.0, 0.4) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_get_proposal(None, ctypes.byref(d)) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_tune_heating(None, 1.5, ctypes.byref(d)) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_tune_from_curve(None, vp(T), vp(T), 2, ctypes.byref(d)) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_energy_curve(8, 8, None, None, vp(T), 0, vp(T)) == mpr.MPR_ERR_INVALID_ARG
+    bad = np.array([0.1, -1.0])
+    assert lib.mpr_energy_curve(8, 8, None, None, vp(bad), 2, vp(T)) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_run_auto(None, 10, 100, 10, None) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_set_sweep_kernel(None, 0) == mpr.MPR_ERR_INVALID_ARG
+    assert lib.mpr_trim_memory() == mpr.MPR_OK   # no pool created yet: nothing to return
