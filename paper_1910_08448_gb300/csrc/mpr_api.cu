@@ -114,6 +114,8 @@ struct mpr_ctx {
     double* acc[2] = {nullptr, nullptr};
     float* acc_hi[2] = {nullptr, nullptr};
     float* acc_lo[2] = {nullptr, nullptr};
+    int* part32[2] = {nullptr, nullptr};   // FP16 spins + FP64 sums: fixed-point partial sums
+    int pending32 = 0;                     // samples in part32 not yet folded into acc
     void* part = nullptr;                // reduction partials
     size_t part_bytes = 0;
     double* scal = nullptr;              // 16 device scalars
@@ -223,6 +225,7 @@ void free_state(mpr_ctx* h)
         dfree(h, &h->acc[c], accd_bytes(h));
         dfree(h, &h->acc_hi[c], accf_bytes(h));
         dfree(h, &h->acc_lo[c], accf_bytes(h));
+        dfree(h, &h->part32[c], accf_bytes(h));
     }
 }
 
@@ -298,6 +301,10 @@ mpr_status init_state(mpr_ctx* h)
         if (p.acc == 0) {
             CHECK(dalloc(h, &h->acc[c], accd_bytes(h)));
             CU(cudaMemsetAsync(h->acc[c], 0, accd_bytes(h), h->stream));
+            if (p.store == kF16 && p.func == 1) {   // exact fixed-point partials (tile kernel)
+                CHECK(dalloc(h, &h->part32[c], accf_bytes(h)));
+                CU(cudaMemsetAsync(h->part32[c], 0, accf_bytes(h), h->stream));
+            }
         } else {
             CHECK(dalloc(h, &h->acc_hi[c], accf_bytes(h)));
             CHECK(dalloc(h, &h->acc_lo[c], accf_bytes(h)));
@@ -324,6 +331,7 @@ mpr_status init_state(mpr_ctx* h)
     h->Nss = (long long)h->host[1];
     h->sweep = 0;
     h->nsamples = 0;
+    h->pending32 = 0;
     h->have_T = false;
     h->T = 0.0;
     h->n_probes = 0;
@@ -430,6 +438,18 @@ mpr_status ensure_eseries(mpr_ctx* h, int n)
     return MPR_OK;
 }
 
+// Adds the fixed-point partial sums (units of 2^-24) into the FP64 sums and clears them; every add
+// is exact, so the sums equal those of adding each sample to FP64 directly.
+mpr_status fold_partials(mpr_ctx* h)
+{
+    if (!h->part32[0] || h->pending32 == 0) return MPR_OK;
+    const size_t n = (size_t)h->L.Ly * h->L.pitch;
+    for (int c = 0; c < 2; ++c) CU(launch_fold_partials(h->acc[c], h->part32[c], n, h->stream));
+    h->launches += 2;
+    h->pending32 = 0;
+    return MPR_OK;
+}
+
 // n hybrid sweeps at temperature T; with kMeasure the raw bond sum of sweep k lands in
 // eseries[k]. Every launch goes to the handle's stream; nothing here synchronises, except the
 // one-time choice of the FP32 sweep kernel (sweep_kind), which waits for its timing events.
@@ -483,6 +503,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
             a.mbits = h->mb[c];
             a.acc = h->acc[c];
             a.acc_hi = h->acc_hi[c];
+            a.part32 = h->part32[c];
             a.acc_lo = h->acc_lo[c];
             if (kind == 1 && h->stall_ns > 0) {   // injected stall: this launch only
                 SweepArgs s = a;
@@ -499,6 +520,8 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
         if (flags & kMeasure) CU(launch_reduce(h->prec, h->part, nblk, h->eseries + k, h->stream));
         if (adapt) CU(launch_adapt_width(h->scal + 14, prop_count(h), h->Np, h->prop_target, h->stream));
         h->launches += ((flags & kMeasure) ? 3 : 2) + (adapt ? 1 : 0);
+        // int32 partials hold at most 16 samples: fold them into the FP64 sums then
+        if ((flags & kSample) && h->part32[0] && ++h->pending32 == 16) CHECK(fold_partials(h));
         ++h->sweep;
         h->site_updates += (uint64_t)h->Np;
         return MPR_OK;
@@ -869,6 +892,7 @@ mpr_status mpr_run_auto(mpr_handle h, int chunk, int max_equil, int samples, int
 
 static mpr_status predict_to(mpr_handle h, double* out_dev)
 {
+    CHECK(fold_partials(h));
     CU(launch_predict(h->L, h->prec, h->z, h->mask, h->scal, h->acc[0], h->acc[1], h->acc_hi[0],
                       h->acc_lo[0], h->acc_hi[1], h->acc_lo[1], h->nsamples, out_dev, h->stream));
     h->launches += 1;

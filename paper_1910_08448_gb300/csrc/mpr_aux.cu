@@ -321,6 +321,21 @@ __global__ void adapt_width_kernel(double* __restrict__ width, unsigned long lon
 
 inline int grid_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
+// Folds fixed-point partial sums of sampled FP16 angles (units of 2^-24) into the FP64 sums:
+// exact, as both are integer multiples of 2^-24 far below 2^53 units.
+__global__ void __launch_bounds__(kThreads) fold_partials_kernel(double* __restrict__ acc,
+                                                                 int* __restrict__ part,
+                                                                 long long n)
+{
+    const long long i = blockIdx.x * (long long)kThreads + threadIdx.x;
+    if (i >= n) return;
+    const int v = part[i];
+    if (v) {
+        acc[i] += (double)v * 0x1.0p-24;
+        part[i] = 0;
+    }
+}
+
 template <typename Fn>
 cudaError_t dispatch_store(int store, Fn&& f)
 {
@@ -453,6 +468,13 @@ cudaError_t launch_adapt_width(double* width, unsigned long long* count, long lo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, adapt_width_kernel, width, count, n_pred, target);
+}
+
+cudaError_t launch_fold_partials(double* acc, int* part, size_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    fold_partials_kernel<<<grid_for((long long)n), kThreads, 0, st>>>(acc, part, (long long)n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed, cudaStream_t st)

@@ -52,6 +52,9 @@ struct SweepArgs {
     double* acc;               // FP64 accumulators of the colour (kSample, acc = FP64)
     float* acc_hi;             // Kahan sum / compensation (kSample, acc = Kahan FP32)
     float* acc_lo;
+    int* part32;               // FP16 spins with FP64 accumulators: exact fixed-point partial sums
+                               // (units of 2^-24) of up to 16 samples, folded into acc by the
+                               // handle; NULL: samples go straight to acc
     void* epart;               // per-block energy partials (kMeasure on colour 1), E type
     int Lx, Ly, Lxh, pitch, mpitch;
     int colour;
@@ -121,6 +124,8 @@ cudaError_t launch_set_state(const Layout& L, const Precision& p, const double* 
                              const unsigned char* mask, void* ang0, void* ang1, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t* out, int n, uint64_t seed,
                           cudaStream_t st);
+// acc[i] += part[i] * 2^-24 and part[i] = 0 for i < n (fixed-point partial sums of FP16 spins).
+cudaError_t launch_fold_partials(double* acc, int* part, size_t n, cudaStream_t st);
 // One step of the proposal-width adaptation (bounded proposals): reads and clears *count.
 cudaError_t launch_adapt_width(double* width, unsigned long long* count, long long n_pred,
                                double target, cudaStream_t st);

@@ -89,7 +89,11 @@ template <typename S, bool PROP>
 cudaError_t dispatch_mode(const Precision& p, const SweepArgs& a, cudaStream_t st)
 {
     const bool measure = (a.flags & kMeasure) && a.colour == 1;
-    const int sample = (a.flags & kSample) ? (p.acc == 0 ? 1 : 2) : 0;
+    const int sample = (a.flags & kSample) ? (p.acc == 0 ? (a.part32 ? 3 : 1) : 2) : 0;
+    if constexpr (sizeof(S) == 2) {   // fixed-point partial sums: FP16 spins only
+        if (sample == 3) return measure ? go<S, true, 3, PROP>(a, st) : go<S, false, 3, PROP>(a, st);
+    }
+    if (sample == 3) return cudaErrorInvalidValue;
     if (measure) {
         if (sample == 0) return go<S, true, 0, PROP>(a, st);
         if (sample == 1) return go<S, true, 1, PROP>(a, st);

@@ -231,3 +231,26 @@ def test_batch_errors_name_the_problem(mpr):
     with pytest.raises(mpr.MPRError) as e:
         mpr.mpr_batch_create([p.z for p in probs], ms, "SDD")
     assert e.value.status == mpr.MPR_ERR_INVALID_ARG
+
+
+def test_fixed_point_sample_sums_equal_fp64_sums(mpr):
+    # A single handle with FP16 spins and FP64 sums adds samples as exact int32 partials (units of
+    # 2^-24) folded into the FP64 sums every 16 samples and before a prediction; the batch adds
+    # each sample to FP64 directly. Both are exact, so predictions agree bit for bit -- across
+    # folds (40 samples), and with a prediction taken in between (after 21).
+    probs = _problems([(300, 200, 0.9), (64, 64, 0.33)], base=500)
+    b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "HDS", seed=13)
+    h = mpr.mpr_create(probs[0].z, probs[0].mask)
+    try:
+        mpr.mpr_batch_fill(b, 10, 40, T=np.full(len(probs), 0.25))
+        mpr.mpr_set_options(h, "HDS", seed=13)
+        mpr.mpr_set_temperature(h, 0.25)
+        mpr.mpr_run(h, 10, 21)
+        mid = mpr.mpr_predict(h)
+        mpr.mpr_run(h, 0, 19)
+        assert np.array_equal(mpr.mpr_predict(h), mpr.mpr_batch_predict(b, 0))
+        assert np.all(np.isfinite(mid))
+        assert mpr.mpr_get_info(h)["n_samples"] == 40
+    finally:
+        mpr.mpr_batch_destroy(b)
+        mpr.mpr_destroy(h)
