@@ -353,8 +353,8 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             // FP16 spins, FP64 sums: f is an FP16 value, an integer multiple of 2^-24 below
             // 2^3, so f * 2^24 converts to an int exactly and 16 of them fit an int32; the
             // handle folds the partial into the FP64 sum, where every add is exact (the sum stays
-            // a multiple of 2^-24 below 2^29): the same bits as adding f itself, in 4 B of
-            // traffic per sample instead of 16
+            // a multiple of 2^-24 below 2^29): the same bits as adding f itself, with a 4-byte
+            // read and write per sample instead of 8-byte ones
             if (upd[k]) a.part32[idx + k] += __float2int_rn(f * 16777216.0f);
         }
         if (MEASURE && ex[k]) {
