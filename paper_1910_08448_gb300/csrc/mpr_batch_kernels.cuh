@@ -455,9 +455,10 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
 }
 
 // ---- graph mode: one launch of a CUDA graph whose while-loop node repeats a red and a black
-// pass kernel and the finish kernel (mpr_batch.cu) on the device until every problem is done. Each pass kernel runs one tile per block (the
-// hardware scheduler overlaps many blocks, hiding each tile's load latency); the finish kernel
-// shrinks the tile list and sets the loop condition. No grid barrier, no spin wait.
+// pass kernel and the finish kernel (mpr_batch.cu) on the device until every problem is done.
+// Each pass kernel runs one tile per block (the hardware scheduler overlaps many blocks, hiding
+// each tile's load latency); the finish kernel shrinks the tile list and sets the loop
+// condition. No grid barrier, no spin wait.
 
 // Compiled for 4 resident blocks per SM: the inlined plain tile (most passes) fits 64 registers;
 // the rarer energy and sampling variants are calls that may spill.
