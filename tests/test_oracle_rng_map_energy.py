@@ -31,6 +31,47 @@ def test_philox4x64_matches_numpy(orc):
         assert np.array_equal(got, exp)
 
 
+def _triton_philox4x32(rounds, cases):
+    """Words of Triton's Philox-4x32 (its CPU interpreter, a fresh process) for each
+    (k0, k1, counters) case; None when Triton is not installed."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    pytest.importorskip("triton")
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, os.path.join(here, "philox_triton_ref.py")],
+                       input=json.dumps({"rounds": rounds, "cases": cases}),
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout)
+
+
+def test_philox4x32_matches_triton(orc):
+    # The 4x32 instance against an implementation written elsewhere: Triton's
+    # triton.language.philox (Salmon et al.'s round function and Weyl key schedule with the
+    # published 32-bit multipliers and constants), executed by Triton's CPU interpreter. Counters
+    # all zero and all ones (key likewise), then random counters under random keys, at the
+    # generator's 10 rounds and at 7 (so the round count itself is pinned). A typo in either
+    # multiplier or Weyl constant, a swapped high/low half of a product, a wrong word permutation
+    # or key bump fails here; the chi-square and avalanche test below would not see them.
+    rng = np.random.default_rng(3)
+    cases = [[0, 0, [[0, 0, 0, 0]]],
+             [0xFFFFFFFF, 0xFFFFFFFF, [[0xFFFFFFFF] * 4]],
+             [0, 0xFFFFFFFF, [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]]]]
+    for _ in range(4):
+        k = rng.integers(0, 2**32, 2)
+        cases.append([int(k[0]), int(k[1]), rng.integers(0, 2**32, (64, 4)).tolist()])
+    for rounds in (10, 7):
+        got = _triton_philox4x32(rounds, cases)
+        for (k0, k1, ctrs), words in zip(cases, got):
+            for c, w in zip(ctrs, words):
+                exp = [int(v) for v in orc.philox(32, rounds, c, [k0, k1])]
+                assert exp == w, (rounds, k0, k1, c, exp, w)
+
+
 def test_philox4x32_uniform_and_avalanche(orc):
     from scipy import stats
 
