@@ -29,11 +29,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SM_COUNT = 152
-# MUFU lanes per SM per clock when the probe cannot run: sin/cos/rcp 16; ex2 32 on this part
-# (the probe measured 15.9 and 31.7 on GB300)
-MUFU_FALLBACK_PER_CLK = {"sin": 16, "cos": 16, "ex2": 32, "rcp": 16}
+# MUFU lanes per SM per clock when the probe cannot run (nominal, times the device's own SM count
+# and maximum clock): 16 for each of sin, cos, ex2 and rcp
+MUFU_FALLBACK_PER_CLK = {"sin": 16, "cos": 16, "ex2": 16, "rcp": 16}
 STORE_BYTES = {"D": 8, "S": 4, "H": 2, "B": 2}
+# Temperature of the oracle's timed sweeps when no tuned value is at hand (--impl reference): the
+# temperature the tuning reaches on the default workload (4096^2, p = 0.9, field seed 1, mask
+# seed 101), T = 0.0649; the measured arm times its cpu_baseline at its own tuned T.
+WORKLOAD_T = 0.065
 
 
 def parse():
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--tune-eq", type=int, default=200, help="sweeps per tuning probe before measuring")
     ap.add_argument("--tune-meas", type=int, default=50, help="measured sweeps per tuning probe")
     ap.add_argument("--ddd-sweeps", type=int, default=10, help="FP64 sweeps timed for the speedup")
+    ap.add_argument("--no-ddd-job", action="store_true",
+                    help="skip the FP64 (DDD) job on the same problem that gives the accuracy gap")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--workload", choices=["single", "batch"], default="single",
                     help="single: one L x L field; batch: many uneven problems in one launch")
@@ -60,6 +65,8 @@ def parse():
                     help="FP32 sweep kernel: -1 automatic (timed per job), 0 tile per block, 1 TMA-fed")
     ap.add_argument("--proposal", default="",
                     help="bounded Metropolis proposals 'WIDTH,TARGET' (mpr_set_proposal); default uniform")
+    ap.add_argument("--ref-T", type=float, default=WORKLOAD_T,
+                    help="--impl reference: temperature of the oracle's timed sweeps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -207,7 +214,7 @@ def stored_counters(kernel_id: str, kernel: str, workload: str):
 SWEEP_KERNELS = {-1: "mpr::sweep_kernel", 0: "mpr::sweep_f32_kernel", 1: "mpr::sweep_f32_tma_kernel"}
 
 
-def mufu_rates(local_rank: int, sm_mhz_max: float):
+def mufu_rates(local_rank: int, sm_mhz_max: float, sm_count: int):
     """Special-function throughput (ops/s) measured by the probe that build() compiles
     (paper_1910_08448_gb300/probe/mufu_rate.cu), on this rank's GPU; nominal lanes x clock if it
     cannot run."""
@@ -224,7 +231,7 @@ def mufu_rates(local_rank: int, sm_mhz_max: float):
             return rates, "probe"
     except (OSError, ValueError, KeyError, IndexError, subprocess.SubprocessError):
         pass
-    return {k: SM_COUNT * v * sm_mhz_max * 1e6 for k, v in MUFU_FALLBACK_PER_CLK.items()}, "nominal"
+    return {k: sm_count * v * sm_mhz_max * 1e6 for k, v in MUFU_FALLBACK_PER_CLK.items()}, "nominal"
 
 
 def peaks():
@@ -334,7 +341,8 @@ def run_mine(args, dist: Dist):
     # MUFU work of one pass: every site's sin/cos once (staged as a neighbour); per prediction
     # site its own sin/cos, the proposal's sin/cos, one ex2 and one rcp. Each at its own measured
     # rate; expressed in sin-equivalent operations at the sin rate.
-    rates, mufu_src = mufu_rates(dist.local, sm_mhz_max)
+    rates, mufu_src = mufu_rates(dist.local, sm_mhz_max,
+                                 torch.cuda.get_device_properties(dev).multi_processor_count)
     r_sc = min(rates["sin"], rates["cos"])
     t_mufu = (N / 2) * (2 / r_sc + p * (4 / r_sc + 1 / rates["ex2"] + 1 / rates["rcp"]))
     mufu_launch = t_mufu * r_sc
@@ -385,6 +393,30 @@ def run_mine(args, dist: Dist):
         ddd = {"fp64_sweep_site_updates_per_s": ddd_rate,
                "sweep_site_updates_per_s": fast_rate, "speedup_vs_fp64_gpu": fast_rate / ddd_rate}
 
+    # ---- the same job in FP64 (DDD) on the same problem and seed, outside the timed region: the
+    # reference of the metric's accuracy clause (MAE of the reduced-precision job within 1 % of
+    # the FP64 job's) ----
+    ddd_job = None
+    if not args.no_ddd_job and args.setup != "DDD":
+        out_d = torch.empty_like(zt)
+        h = mpr.mpr_create_dev(zt, mt)
+        try:
+            mpr.mpr_set_options(h, "DDD", seed=seed)
+            if proposal:
+                mpr.mpr_set_proposal(h, *proposal)
+            mpr.mpr_set_tuning(h, n_eq=args.tune_eq, n_meas=args.tune_meas)
+            t0 = time.perf_counter()
+            T_d, _ = mpr.mpr_tune_temperature(h)
+            mpr.mpr_run(h, args.equil, args.samples)
+            mpr.mpr_predict_dev(h, out_d)
+            info_d = mpr.mpr_get_info(h)
+            torch.cuda.synchronize()
+            t_d = time.perf_counter() - t0
+        finally:
+            mpr.mpr_destroy(h)
+        ddd_job = {"zhat": out_d.cpu().numpy(), "T": T_d, "e_bond_mean": info_d["e_bond_mean"],
+                   "seconds": t_d, "site_updates": info_d["site_updates"]}
+
     # ---- end to end through the host API: pinned inputs, H2D + D2H inside the timing ----
     e2e = None
     if not args.no_e2e:
@@ -430,6 +462,18 @@ def run_mine(args, dist: Dist):
     acc_rep = {"mae": float(np.mean(np.abs(err))), "rmse": float(np.sqrt(np.mean(err ** 2))),
                "T": T_last, "e_bond_mean": infos[-1]["e_bond_mean"],
                "e_sample": infos[-1]["e_sample"]}
+    if ddd_job is not None:
+        err_d = (ddd_job["zhat"] - pr.z)[pred]
+        mae_d = float(np.mean(np.abs(err_d)))
+        rmse_d = float(np.sqrt(np.mean(err_d ** 2)))
+        acc_rep.update({
+            "mae_fp64_gpu": mae_d, "rmse_fp64_gpu": rmse_d, "T_fp64_gpu": ddd_job["T"],
+            "e_bond_fp64_gpu": ddd_job["e_bond_mean"],
+            # relative gaps of this setup's job to the FP64 job (same problem, seed and sweeps)
+            "mae_gap": acc_rep["mae"] / mae_d - 1.0, "rmse_gap": acc_rep["rmse"] / rmse_d - 1.0,
+            "e_bond_gap": acc_rep["e_bond_mean"] / ddd_job["e_bond_mean"] - 1.0,
+            "fp64_job_seconds": ddd_job["seconds"],
+            "fp64_job_site_updates_per_s": ddd_job["site_updates"] / ddd_job["seconds"]})
 
     return {
         "value": value, "ms": ms, "updates": updates, "launches": launches, "roof": roof,
@@ -518,8 +562,9 @@ def run_batch(args, dist):
             "sweeps_per_problem": [int(np.min(sweeps)), int(np.median(sweeps)), int(np.max(sweeps))]}
 
 
-def oracle_sample(L, p, setup, seconds, seed=7, pr=None):
-    """The FP64 oracle, as it stands, on a bounded number of sweeps of the same workload."""
+def oracle_sample(L, p, setup, seconds, seed=7, pr=None, T=None):
+    """The FP64 oracle, as it stands, on a bounded number of sweeps of the same workload at the
+    job's temperature T."""
     import mpr_inputs
     import oracle
 
@@ -531,20 +576,21 @@ def oracle_sample(L, p, setup, seconds, seed=7, pr=None):
     phi = o.init(phi, pr.mask)
     n_pred = int((pr.mask == 0).sum())
     t0 = time.perf_counter()
-    phi, _, _ = o.run(phi, pr.mask, 0.5, 0, 1)
+    T = WORKLOAD_T if T is None else T
+    phi, _, _ = o.run(phi, pr.mask, T, 0, 1)
     t1 = time.perf_counter() - t0
     n = max(1, int(seconds / max(t1, 1e-9)) - 1)
     t0 = time.perf_counter()
-    o.run(phi, pr.mask, 0.5, 1, n)
+    o.run(phi, pr.mask, T, 1, n)
     t = time.perf_counter() - t0
     return {"value": n * n_pred / t, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} hybrid sweeps of the {L}x{L} p={p} lattice at T=0.5 "
+            "sample": f"{n} hybrid sweeps of the {L}x{L} p={p} lattice at T={T:.4g} "
                       f"({n * n_pred} site-updates, {t:.1f} s, 1 thread)"}
 
 
 def _oracle_worker(args):
     """One oracle replica for the all-cores sample: its own chain (seed) on the shared problem."""
-    zpath, mpath, L, setup, seed, n, barrier, queue = args
+    zpath, mpath, L, setup, seed, n, T, barrier, queue = args
     import numpy as np
 
     import oracle
@@ -555,10 +601,10 @@ def _oracle_worker(args):
     phi, _, _ = o.map(z, mask)
     phi = o.init(phi, mask)
     n_pred = int((mask == 0).sum())
-    phi, _, _ = o.run(phi, mask, 0.5, 0, 1)   # warm-up sweep (page-in), untimed
+    phi, _, _ = o.run(phi, mask, T, 0, 1)   # warm-up sweep (page-in), untimed
     barrier.wait()
     t0 = time.monotonic()
-    o.run(phi, mask, 0.5, 1, n)
+    o.run(phi, mask, T, 1, n)
     queue.put((n * n_pred, t0, time.monotonic()))
 
 
@@ -569,7 +615,7 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7):
+def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7, T=None):
     """The oracle as it stands on every host core at once: one independent replica (own chain) per
     process, all started together behind a barrier; value = all site-updates / the wall time from
     the first start to the last finish (CLOCK_MONOTONIC is shared by the processes). Processes
@@ -583,7 +629,8 @@ def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7):
     import oracle
 
     oracle.build()
-    single = oracle_sample(L, p, setup, min(seconds, 6.0), seed=seed, pr=pr)
+    T = WORKLOAD_T if T is None else T
+    single = oracle_sample(L, p, setup, min(seconds, 6.0), seed=seed, pr=pr, T=T)
     workers = workers or host_cores()
     # memory guard: each replica holds the data and about two copies of the state (FP64); use at
     # most a quarter of the host's available memory
@@ -609,7 +656,7 @@ def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7):
         barrier = ctx.Barrier(workers)
         queue = ctx.Queue()
         procs = [ctx.Process(target=_oracle_worker,
-                             args=((zpath, mpath, L, setup, seed + 1 + i, n, barrier, queue),))
+                             args=((zpath, mpath, L, setup, seed + 1 + i, n, T, barrier, queue),))
                  for i in range(workers)]
         for pr_ in procs:
             pr_.start()
@@ -622,7 +669,7 @@ def oracle_sample_cores(L, p, setup, seconds, pr, workers=None, seed=7):
     wall = max(r[2] for r in res) - min(r[1] for r in res)
     return {"value": upd / wall, "unit": "site-updates/s", "cores": workers, "kind": "oracle",
             "sample": f"{workers} processes, each {n} hybrid sweeps of its own chain on the {L}x{L} "
-                      f"p={p} lattice at T=0.5 ({upd} site-updates in {wall:.1f} s wall)",
+                      f"p={p} lattice at T={T:.4g} ({upd} site-updates in {wall:.1f} s wall)",
             "single_thread": {"value": single["value"], "sample": single["sample"]}}
 
 
@@ -649,10 +696,10 @@ def main():
             vals = []
             # warm-up steps: one single-thread sample each (pages the oracle and the data in)
             for k in range(args.warmup):
-                oracle_sample(args.L, args.p, args.setup, 2.0, pr=pr)
+                oracle_sample(args.L, args.p, args.setup, 2.0, pr=pr, T=args.ref_T)
             for k in range(args.steps):
                 vals.append(oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds / 2,
-                                                pr))
+                                                pr, T=args.ref_T))
             v = statistics.mean(r["value"] for r in vals)
             line = {"metric": metric, "value": v, "unit": "site-updates/s", "n_gpus": args.gpus,
                     "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -702,7 +749,8 @@ def main():
     res = run_mine(args, dist)
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
-        cpu = oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds, res["problem"])
+        cpu = oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds, res["problem"],
+                                  T=res["accuracy"]["T"])
     if dist.rank == 0:
         line = {
             "metric": metric, "value": res["value"], "unit": "site-updates/s",

@@ -293,16 +293,20 @@ mpr_status mpr_batch_inject_barrier_fault(mpr_batch b, int extra_arrivals, doubl
 
 /* mpr_bond_energy_noalloc: e_bond = -(1/N_b) sum_<ij> cos[q(phi_i - phi_j)] of a state the caller
  * holds on the device, computed without allocating any device memory. The paper has no
- * counterpart; this entry point exists for callers that cannot call cudaMalloc -- code running
- * while a CUDA graph is captured, code under a fixed device-memory budget or a custom allocator
- * that owns the device, real-time loops that must not take allocator locks or synchronise.
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc -- code under a
+ * fixed device-memory budget or a custom allocator that owns the device, real-time loops that must
+ * not take allocator locks or synchronise.
  *   angles_dev: Lx*Ly doubles, row-major, device memory (every site, frozen or not).
  *   e_bond_dev: one double in device memory, written on `stream` (a cudaStream_t, NULL = legacy
  *               default stream); the call returns once the work is queued.
  * Limit: Lx*Ly <= 2^28 sites (16384 x 16384); larger grids return MPR_ERR_INVALID_ARG. The scratch
  * is a fixed 32 KiB array inside the library that every GPU loading the library holds until the
- * process exits. The first call on a device looks up that array's device address (so make it
- * before any stream capture that should contain later calls). All calls share the array: calls
+ * process exits. The first call on a device looks up that array's device address in the current
+ * (primary) context of the device and caches it per device for the life of the process (so make
+ * that first call before any stream capture that should contain later calls). The cache is not
+ * refreshed: after cudaDeviceReset on a device, which destroys that context, the cached address is
+ * stale, and this entry point must not be called on that device again in the same process.
+ * All calls share the array: calls
  * that overlap on the GPU (e.g. on two streams) race and must be ordered by the caller.
  * No cudaMalloc, cudaFree or other allocating call is made. */
 mpr_status mpr_bond_energy_noalloc(int Lx, int Ly, const double* angles_dev, double q,

@@ -372,7 +372,8 @@ def mpr_philox4x32_10_dev(ctr, seed: int, stream=None):
 
 def mpr_bond_energy_noalloc(angles, q: float, out, stream=None):
     """Bond energy of a state held on the device, with no device allocation (for callers that
-    cannot allocate, e.g. inside CUDA-graph capture). angles: (Ly, Lx) float64 CUDA tensor;
+    cannot allocate: device memory owned by another allocator or a fixed budget, loops that must
+    not take the allocator's locks). angles: (Ly, Lx) float64 CUDA tensor;
     out: float64 CUDA tensor of at least one element, written asynchronously on ``stream``."""
     if angles.dim() != 2:
         raise ValueError("angles must be a 2-D tensor (Ly, Lx)")

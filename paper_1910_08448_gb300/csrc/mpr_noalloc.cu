@@ -1,9 +1,8 @@
 // mpr_noalloc.cu -- mpr_bond_energy_noalloc: the bond energy of a caller-held state with no device
 // allocation at all.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured (an
-// allocation would break or end the capture), code that works under a strict device-memory budget
-// or a custom allocator that owns the whole device, and real-time loops that must not take the
+// Some callers cannot call cudaMalloc: code that works under a strict device-memory budget or a
+// custom allocator that owns the whole device, and real-time loops that must not take the
 // allocator's locks or synchronise. Every other entry point of this library allocates its scratch
 // (reduction partials) inside a handle. This one keeps its scratch in a fixed array compiled into
 // the library instead, so a call only launches kernels.
@@ -74,7 +73,9 @@ __global__ void __launch_bounds__(kThreads) bond_final(const double* __restrict_
 }
 
 // Device address of g_bond_partials per device. In host code the array's name only stands for
-// the symbol, so the address is looked up once per device, with that device current, and cached.
+// the symbol, so the address is looked up once per device, with that device current, and cached
+// for the life of the process. It belongs to the device's primary context: after a
+// cudaDeviceReset of that device the cached address is stale (see include/mpr.h).
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 

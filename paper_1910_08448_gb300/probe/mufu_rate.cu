@@ -2,8 +2,8 @@
 // sin.approx, cos.approx, ex2.approx and rcp.approx (the reciprocal inside the FP32 quotient), in
 // operations per second on device 0. Measurement infrastructure for the roofline of bench.py (the
 // peaks file holds no MUFU figure): every thread runs 8 independent chains of one operation each,
-// on 8 resident blocks per SM, after a warm-up that brings the clocks up; the best of three timed
-// runs counts. Prints one JSON object.
+// with finite, normal operands throughout, on 8 resident blocks per SM, after a warm-up that
+// brings the clocks up; the best of three timed runs counts. Prints one JSON object.
 #include <cstdio>
 #include <cuda_runtime.h>
 
@@ -23,10 +23,14 @@ __global__ void __launch_bounds__(256) chains(float* out, int iters)
             if (OP == 1) asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[i]));
             if (OP == 2) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[i]));
             if (OP == 3) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[i]));
-            // sin, cos and ex2 feed their result straight back (sin/cos stay in [-1, 1]; ex2
-            // saturates at +inf, which the unit handles at the same rate); rcp gets one
-            // dependent FMA, so that no two reciprocals can be folded into one another
-            a[i] = OP == 3 ? y * 0.5f + 0.25f : y;
+            // every operand stays a finite normal number in the range the sweep uses. sin and
+            // cos feed their result straight back (the iterates stay in (0, 1)); ex2 feeds back
+            // -2y, so 2^a converges to 1/2 with a in [-2.4, 0) and never reaches a special
+            // operand (inf, 0 or a subnormal, which the unit may pass through at another rate);
+            // rcp gets one dependent FMA (the iterate settles near 0.84), so no two reciprocals
+            // can be folded into one another. sin and cos, like the sweep's, carry the one
+            // multiply of their range scaling
+            a[i] = OP == 3 ? y * 0.5f + 0.25f : (OP == 2 ? -2.0f * y : y);
         }
     }
     float s = 0.f;

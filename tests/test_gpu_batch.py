@@ -45,7 +45,7 @@ def _neighbours(b):
 
 
 @pytest.mark.parametrize("setup", ["SDS", "HDS", "SSS"])
-def test_batch_single_sweep_matches_oracle_per_problem(mpr, orc, setup):
+def test_batch_single_sweep_matches_oracle_per_problem(mpr, orc, excusal_log, setup):
     probs = _problems()
     b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], setup, seed=17)
     try:
@@ -72,12 +72,18 @@ def test_batch_single_sweep_matches_oracle_per_problem(mpr, orc, setup):
             # red sites whose stored result differs from the oracle's by more than FP32 error (a
             # 16-bit rounding that went the other way): their black neighbours see other inputs
             differs = bad_r | ((col == 0) & (np.abs(got - red_r) > 1e-4))
-            assert differs.mean() < 0.01
+            # bounds about 3x the measured rates (as in the single-handle 16-bit test)
+            red_b, black_b = (0.01, 0.045) if setup[0] == "H" else (0.0025, 0.01)
+            assert differs.sum() <= max(2, red_b * (col == 0).sum())
             excused = ((col == 1) & ((mm_b < 1e-4) | (om_b < 1e-4))) | (_neighbours(differs) & (col == 1))
             sel = (col == 1) & ~excused
             d = np.abs(got - rnd(blk))
             assert np.all(d[sel] <= ulp + 1e-4), (i, d[sel].max())
-            assert excused[col == 1].mean() < 0.05
+            excusal_log(f"{setup} p{i} red", differs.sum(), (col == 0).sum(),
+                        max(2, red_b * (col == 0).sum()))
+            excusal_log(f"{setup} p{i} blk", excused[col == 1].sum(), (col == 1).sum(),
+                        max(8, black_b * (col == 1).sum()))
+            assert excused[col == 1].sum() <= max(8, black_b * (col == 1).sum())
             m = pr.mask == 1
             assert np.array_equal(got[m], start[m])
     finally:

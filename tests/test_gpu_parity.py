@@ -167,7 +167,7 @@ def _gpu_sweeps(mpr, pr, setup, seed, state, sweep, T, equil, samples=0):
 
 @pytest.mark.parametrize("Lx,Ly,p", SHAPES)
 @pytest.mark.parametrize("T", [0.08, 1.0])
-def test_single_sweep_ddd(mpr, orc, Lx, Ly, p, T):
+def test_single_sweep_ddd(mpr, orc, excusal_log, Lx, Ly, p, T):
     pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=5, mask_seed=6)
     o, state = _start_state(orc, pr, "DDD", 99)
     got, sw, info, _, _ = _gpu_sweeps(mpr, pr, "DDD", 99, state, 17, T, 1)
@@ -177,7 +177,9 @@ def test_single_sweep_ddd(mpr, orc, Lx, Ly, p, T):
     excused = bad | (_neighbours(bad & (_colour(Lx, Ly) == 0)) & (_colour(Lx, Ly) == 1))
     d = np.abs(got - exp)
     assert np.all(d[~excused] <= 1e-9), d[~excused].max()
-    assert excused.sum() <= max(2, 1e-4 * Lx * Ly)
+    # FP64 margins below 1e-11 are rare (< 1e-5 of the sites)
+    excusal_log("DDD", excused.sum(), Lx * Ly, 1e-5 * Lx * Ly)
+    assert excused.sum() <= 1e-5 * Lx * Ly
     m = pr.mask == 1
     assert np.array_equal(got[m].view(np.uint64), state[m].view(np.uint64))
 
@@ -187,7 +189,7 @@ def test_single_sweep_ddd(mpr, orc, Lx, Ly, p, T):
 @pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (257, 129, 0.66),
                                      (300, 45, 0.66), (2100, 1300, 0.9)])
 @pytest.mark.parametrize("setup", ["SDS", "SSS", "SDD", "DDS"])
-def test_single_sweep_fp32_functions(mpr, orc, Lx, Ly, p, setup):
+def test_single_sweep_fp32_functions(mpr, orc, excusal_log, Lx, Ly, p, setup):
     T = 0.3
     pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=7, mask_seed=8)
     o, state = _start_state(orc, pr, setup, 5)
@@ -199,13 +201,17 @@ def test_single_sweep_fp32_functions(mpr, orc, Lx, Ly, p, setup):
     excused = bad | (_neighbours(bad & (_colour(Lx, Ly) == 0)) & (_colour(Lx, Ly) == 1))
     d = np.abs(got - exp)
     assert np.all(d[~excused] <= tol + 2 * _ulp_store(setup)), d[~excused].max()
-    assert excused.sum() <= max(3, 2e-3 * Lx * Ly)
+    # the excused set comes from the oracle's margins alone (inputs fixed by the seeds); measured
+    # 4.6e-4 of the sites at 2100 x 1300, 1.9e-3 at 131 x 37: the bound is about 3x that
+    bound = max(10, 1.5e-3 * Lx * Ly)
+    excusal_log(setup, excused.sum(), Lx * Ly, bound)
+    assert excused.sum() <= bound
 
 
 @pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (300, 45, 0.66),
                                      (2100, 1300, 0.9)])
 @pytest.mark.parametrize("setup", ["HDS", "BDS", "HSS"])
-def test_single_sweep_16bit_storage(mpr, orc, Lx, Ly, p, setup):
+def test_single_sweep_16bit_storage(mpr, orc, excusal_log, Lx, Ly, p, setup):
     # Red phase: identical inputs; the GPU result is its FP32 update rounded to the storage type.
     # Black phase: against the oracle's black update on the oracle's own red result rounded to the
     # storage type. Both sides round FP32/FP64 red results to the same 16-bit value except near a
@@ -224,14 +230,21 @@ def test_single_sweep_16bit_storage(mpr, orc, Lx, Ly, p, setup):
     d = np.abs(got - red_r)
     assert np.all(d[sel] <= ulp + 1e-4), d[sel].max()
     differs = (col == 0) & (bad_r | (got != red_r))
-    assert differs.mean() < 0.01
+    assert differs.sum() <= (0.01 if setup[0] == "H" else 0.0025) * (col == 0).sum()
     blk, mm_b, om_b = o.half_sweep(red_r, pr.mask, T, 40, 1)
     bad_b = (mm_b < 1e-4) | (om_b < 1e-4)
     excused = bad_b | (_neighbours(differs) & (col == 1))
     sel = (col == 1) & ~excused
     d = np.abs(got - _round_store(blk, setup))
     assert np.all(d[sel] <= ulp + 1e-4), d[sel].max()
-    assert excused[col == 1].mean() < 0.05
+    # red sites whose stored result differs from the oracle's rounded one (a 16-bit rounding that
+    # went the other way, or a decision within the margin) and the black sites they excuse:
+    # measured up to 3.8e-3 / 1.5e-2 of the sites (FP16), 9e-4 / 3.4e-3 (BF16); bounds about 3x
+    red_b, black_b = (0.01, 0.045) if setup[0] == "H" else (0.0025, 0.01)
+    excusal_log(setup + " red", differs.sum(), (col == 0).sum(), red_b * (col == 0).sum())
+    excusal_log(setup + " black", excused[col == 1].sum(), (col == 1).sum(),
+                black_b * (col == 1).sum())
+    assert excused[col == 1].mean() < black_b
 
 
 # --- energies, trajectories, predictions ---------------------------------------------------
@@ -461,7 +474,7 @@ def test_checkpoint_resume_is_bit_exact(mpr, setup):
 
 @pytest.mark.parametrize("q", [0.3, 1.0])
 @pytest.mark.parametrize("setup", ["DDD", "SDS"])
-def test_single_sweep_other_q(mpr, orc, setup, q):
+def test_single_sweep_other_q(mpr, orc, excusal_log, setup, q):
     # the general over-relaxation (any q in (0, 1]; q = 1 is the planar rotator of Eq. 1)
     T = 0.4
     pr = mpr_inputs.make_problem(131, 37, 0.66, field_seed=23, mask_seed=24)
@@ -487,7 +500,9 @@ def test_single_sweep_other_q(mpr, orc, setup, q):
     excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
     d = np.abs(got - exp)
     assert np.all(d[~excused] <= tol + 2 * _ulp_store(setup)), d[~excused].max()
-    assert excused.mean() < 0.01
+    bound = 1e-5 * excused.size if setup == "DDD" else max(10, 1.5e-3 * excused.size)
+    excusal_log(f"{setup} q={q}", excused.sum(), excused.size, bound)
+    assert excused.sum() <= bound
     assert abs(e_s - o.energy_sample(phi, pr.mask)[0]) < 1e-12
 
 
@@ -621,7 +636,7 @@ def test_tma_wait_timeout_is_reported(mpr, orc):
 # --- the bench's workloads at full size, sampled --------------------------------------------
 
 @pytest.mark.parametrize("L,setup", [(4096, "HDS"), (16384, "SDS")])
-def test_full_size_sweep_sampled_sites(mpr, orc, L, setup):
+def test_full_size_sweep_sampled_sites(mpr, orc, excusal_log, L, setup):
     # The workloads bench.py times (4096^2 and 16384^2, p = 0.9) through the C ABI in its launch
     # configuration (the tile kernel, which the automatic choice keeps at these sizes): one sweep
     # from an identical state; 2000 sampled sites of each colour are recomputed one by one by the
@@ -669,9 +684,12 @@ def test_full_size_sweep_sampled_sites(mpr, orc, L, setup):
             if abs(got[y, x] - _round_store(np.array([f]), setup)[0]) > tol:
                 bad += 1
         assert bad == 0, (c, bad)
-        assert excused < 40, (c, excused)
+        # about 1 of 2000 expected (margins below 1e-4 on ~5e-4 of the sites); measured 0
+        excusal_log(f"{setup} c{c}", excused, 2000, 10)
+        assert excused <= 10, (c, excused)
 
 
+@pytest.mark.slow
 def test_maximum_lattice_size(mpr, orc):
     # The largest lattice the ABI accepts (N < 2^31 sites: 65536 x 32767 = 2 147 418 112), HDS,
     # inputs on the device: every element offset beyond 2^31 bytes (FP64 inputs, accumulators,

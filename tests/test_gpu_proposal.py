@@ -84,7 +84,7 @@ def _gpu(mpr, pr, setup, seed, state, sweep, T, width, target, n, kernel=-1):
 @pytest.mark.parametrize("Lx,Ly,p", [(131, 37, 0.9), (300, 45, 0.66), (1100, 300, 0.9)])
 @pytest.mark.parametrize("width", [0.4, 2.5])
 @pytest.mark.parametrize("setup", ["DDD", "SDS"])
-def test_bounded_single_sweep(mpr, orc, Lx, Ly, p, width, setup):
+def test_bounded_single_sweep(mpr, orc, excusal_log, Lx, Ly, p, width, setup):
     T = 0.3
     pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=11, mask_seed=12)
     o, state = _start(orc, pr, setup, 21, width)
@@ -98,7 +98,11 @@ def test_bounded_single_sweep(mpr, orc, Lx, Ly, p, width, setup):
     excused = bad | (_neighbours(bad & (col == 0)) & (col == 1))
     d = np.abs(got - exp)
     assert np.all(d[~excused] <= tol), d[~excused].max()
-    assert excused.sum() <= max(3, 2e-3 * Lx * Ly)
+    # measured: 0 (DDD); up to 8.3e-4 of the sites (SDS); bounds: the survey's 1e-5 for FP64,
+    # about 3x the measured rate otherwise
+    bound = 1e-5 * Lx * Ly if setup == "DDD" else max(10, 1.5e-3 * Lx * Ly)
+    excusal_log(f"{setup} w={width}", excused.sum(), Lx * Ly, bound)
+    assert excused.sum() <= bound
     m = pr.mask == 1
     assert np.array_equal(got[m], state[m])
 
