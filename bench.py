@@ -67,6 +67,9 @@ def parse():
                     help="bounded Metropolis proposals 'WIDTH,TARGET' (mpr_set_proposal); default uniform")
     ap.add_argument("--ref-T", type=float, default=WORKLOAD_T,
                     help="--impl reference: temperature of the oracle's timed sweeps")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the short runs of the batch workload (config 4) and the 16384^2 "
+                         "field (config 5) that the default line reports beside the main number")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -562,6 +565,46 @@ def run_batch(args, dist):
             "sweeps_per_problem": [int(np.min(sweeps)), int(np.median(sweeps)), int(np.max(sweeps))]}
 
 
+def run_extra_configs(args, dist):
+    """Short runs of the two other workloads that are not the metric's own, reported as sub-objects
+    of the default line: the batch of 256 uneven problems (config 4, HDS, tune + 2000 + 200 per
+    problem, one step after one warm-up step) and the 16384^2 field (config 5, SDS, FP64
+    accumulators, tune + 500 + 100, one step after one warm-up step). Each is timed like its own
+    bench line (python bench.py --workload batch; python bench.py --L 16384 --setup SDS --equil
+    500 --samples 100), with fewer steps."""
+    import copy
+
+    out = {}
+    a = copy.copy(args)
+    a.workload, a.steps, a.warmup = "batch", 1, 1
+    b = run_batch(a, dist)
+    out["batch"] = {"config": "4: 256 problems, side log-uniform 64..1024, aspect <= 4:1, "
+                              "p in {0.33,0.66,0.9}, kappa in [0.05,0.5]; tune + 2000 + 200",
+                    "setup": a.setup, "value": b["value"], "unit": "site-updates/s",
+                    "ms_per_step": b["ms"], "steps": 1, "warmup": 1,
+                    "tile_rows_x_cols": b["tile"], "blocks_per_sm": b["blocks_per_sm"],
+                    "mode": ["persistent cooperative kernel", "persistent kernel in a one-node graph",
+                             "graph with device-side while loop"][b["mode"]],
+                    "pred_sites": b["pred_sites"], "sites": b["sites"],
+                    "mean_mae": b["mean_mae"],
+                    "fixed_T_site_updates_per_s": b["fixed_T_fill"]["site_updates_per_s"],
+                    "clocks": b["clocks"]}
+    a = copy.copy(args)
+    a.L, a.setup, a.equil, a.samples = 16384, "SDS", 500, 100
+    a.steps, a.warmup, a.no_e2e, a.no_ddd_job, a.ddd_sweeps = 1, 1, True, True, 0
+    r = run_mine(a, dist)
+    out["config5"] = {"config": "5: 16384x16384, 90% removed, SDS (FP32 spins, FP64 energy and "
+                                "accumulators); tune + 500 + 100",
+                      "value": r["value"], "unit": "site-updates/s", "ms_per_step": r["ms"],
+                      "steps": 1, "warmup": 1,
+                      "roofline": {k: r["roof"][k] for k in ("bound", "achieved", "peak", "unit",
+                                                             "frac", "hbm_frac", "mufu_frac",
+                                                             "launch_us", "kernel")},
+                      "mae": r["accuracy"]["mae"], "T": r["accuracy"]["T"],
+                      "clocks": r["clocks"]}
+    return out
+
+
 def oracle_sample(L, p, setup, seconds, seed=7, pr=None, T=None):
     """The FP64 oracle, as it stands, on a bounded number of sweeps of the same workload at the
     job's temperature T."""
@@ -747,6 +790,9 @@ def main():
         return
 
     res = run_mine(args, dist)
+    extra = {}
+    if dist.world == 1 and args.workload == "single" and not args.no_extra_configs and args.L == 4096:
+        extra = run_extra_configs(args, dist)
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         cpu = oracle_sample_cores(args.L, args.p, args.setup, args.cpu_seconds, res["problem"],
@@ -768,6 +814,7 @@ def main():
             # prediction and release
             "phases_ms": res["phases_ms"],
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     dist.close()
 

@@ -82,6 +82,8 @@ def lib():
             L.mpro_site_words.restype = None
             L.mpro_uniform.argtypes = [P(Cfg), u32]
             L.mpro_uniform.restype = d
+            L.mpro_site_uniforms.argtypes = [P(Cfg), i, i, u32, P(d), P(d)]
+            L.mpro_site_uniforms.restype = None
             L.mpro_map.argtypes = [i, vp, vp, vp, P(d), P(d)]
             L.mpro_map.restype = i
             L.mpro_init.argtypes = [P(Cfg), vp, vp]
@@ -181,6 +183,13 @@ class Oracle:
 
     def uniform(self, w: int) -> float:
         return lib().mpro_uniform(ctypes.byref(self.cfg), w)
+
+    def site_uniforms(self, x: int, y: int, sweep: int):
+        """(proposal, acceptance) uniforms of the Metropolis move of site (x, y) at a sweep."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        lib().mpro_site_uniforms(ctypes.byref(self.cfg), x, y, sweep, ctypes.byref(a),
+                                 ctypes.byref(b))
+        return a.value, b.value
 
     # --- mapping and state ------------------------------------------------------------------
     def map(self, z, mask):

@@ -113,6 +113,59 @@ double mpro_uniform(const mpro_cfg* cfg, uint32_t w)
     return (double)(w >> 9) * (1.0 / 8388608.0);
 }
 
+/* The two Metropolis uniforms of site (x, y) at a sweep: proposal and acceptance, in [0, 1).
+ *
+ * FP64 function setting (ubits = 32): the site's two words from mpro_site_words (tag 0), all 32
+ * bits of each.
+ *
+ * FP32 function setting (ubits = 23): each uniform has 23 bits, so one Philox-4x32-10 call (128
+ * bits) can serve more than two sites. Reading: three calls serve a group of eight same-colour
+ * sites, the four half-lattice columns j = 4g .. 4g + 3 (j = x >> 1) of the two rows 2h and
+ * 2h + 1; call m (m = 0, 1, 2) has counter (g, h, sweep, problem << 8 | m << 2 | colour) and
+ * key = seed, and gives the words W[4m] .. W[4m + 3]. In the group's first row, the one with
+ * y + colour even, site i = j & 3 takes the top 23 bits of W[2i] for its proposal and of
+ * W[2i + 1] for its acceptance. In the second row site i takes the top 23 bits of W[8 + i] for
+ * its proposal, and for its acceptance the 23 bits
+ *     b[3i] | b[3i + 1] << 8 | (b[3i + 2] & 127) << 16,   b[k] = W[k] & 255,
+ * built from the low bytes, which the top-23-bit fields never touch. No bit of the 384 serves two
+ * uniforms. */
+void mpro_site_uniforms(const mpro_cfg* cfg, int x, int y, uint32_t sweep, double* u_prop,
+                        double* u_acc)
+{
+    if (cfg->ubits == 32) {
+        uint32_t wp, wa;
+        mpro_site_words(cfg, x, y, sweep, 0, &wp, &wa);
+        *u_prop = mpro_uniform(cfg, wp);
+        *u_acc = mpro_uniform(cfg, wa);
+        return;
+    }
+    const int c = (x + y) & 1;
+    const int j = x >> 1;
+    const int g = j >> 2, i = j & 3;
+    const int second_row = (y + c) & 1;
+    uint64_t W[12], key[2];
+    key[0] = cfg->seed & 0xffffffffu;
+    key[1] = cfg->seed >> 32;
+    for (int m = 0; m < 3; ++m) {
+        uint64_t ctr[4];
+        ctr[0] = (uint64_t)g;
+        ctr[1] = (uint64_t)(y >> 1);
+        ctr[2] = (uint64_t)sweep;
+        ctr[3] = ((uint64_t)cfg->problem << 8) | ((uint64_t)m << 2) | (uint64_t)c;
+        mpro_philox(32, 10, ctr, key, W + 4 * m);
+    }
+    uint64_t mp, ma;
+    if (!second_row) {
+        mp = W[2 * i] >> 9;
+        ma = W[2 * i + 1] >> 9;
+    } else {
+        mp = W[8 + i] >> 9;
+        ma = (W[3 * i] & 255u) | ((W[3 * i + 1] & 255u) << 8) | ((W[3 * i + 2] & 127u) << 16);
+    }
+    *u_prop = (double)mp * (1.0 / 8388608.0);
+    *u_acc = (double)ma * (1.0 / 8388608.0);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Data -> spins (Sec. 2: the measured data are mapped onto spins).                            */
 /* Reading: phi = 2*pi*(z - zmin)/(zmax - zmin), zmin/zmax over the measured values only.      */
@@ -217,10 +270,8 @@ double mpro_update_site(const mpro_cfg* cfg, const double* phi, const uint8_t* m
      * move is accepted when dE <= 0 or u < exp(-dE/T) (strict). Option (cfg->width > 0): a
      * proposal f + w*(2u - 1) uniform on the segment of half-width w around f (symmetric, so the
      * same acceptance rule holds), rejected when it leaves the state space [0, 2*pi). */
-    uint32_t wp, wa;
-    mpro_site_words(cfg, x, y, sweep, 0, &wp, &wa);
-    double u_prop = mpro_uniform(cfg, wp);
-    double u_acc = mpro_uniform(cfg, wa);
+    double u_prop, u_acc;
+    mpro_site_uniforms(cfg, x, y, sweep, &u_prop, &u_acc);
     double f = phi[s];
     const int bounded = cfg->width > 0.0;
     double f_prop = bounded ? f + cfg->width * (2.0 * u_prop - 1.0) : TWO_PI * u_prop;

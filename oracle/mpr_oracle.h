@@ -28,7 +28,8 @@ typedef struct {
     double q;            /* exponent of Eq. 2, q in (0, 1/2]; q = 1 is the planar rotator of Eq. 1 */
     uint64_t seed;       /* Philox key (low word, high word) */
     uint32_t problem;    /* problem id, part of the Philox counter */
-    int ubits;           /* uniform resolution: 32 -> u = w*2^-32, 23 -> u = (w>>9)*2^-23 */
+    int ubits;           /* uniform resolution: 32 -> u = w*2^-32, 23 -> 23-bit uniforms
+                            (initial angles: (w>>9)*2^-23; Metropolis: mpro_site_uniforms) */
     double width;        /* Metropolis proposal: 0 -> uniform angle on [0, 2*pi); w > 0 ->
                             phi + w*(2u - 1), rejected outside [0, 2*pi) */
 } mpro_cfg;
@@ -53,6 +54,11 @@ void mpro_philox_n(int W, int rounds, int n, const uint64_t* ctr, const uint64_t
 void mpro_site_words(const mpro_cfg* cfg, int x, int y, uint32_t sweep, int tag,
                      uint32_t* w_prop, uint32_t* w_acc);
 double mpro_uniform(const mpro_cfg* cfg, uint32_t w);
+/* The Metropolis uniforms (proposal, acceptance) of site (x, y) at a sweep: from the site's two
+ * words with ubits = 32; with ubits = 23 from three Philox calls per group of eight same-colour
+ * sites (four half-lattice columns x two rows), 23 bits each (layout in mpr_oracle.c). */
+void mpro_site_uniforms(const mpro_cfg* cfg, int x, int y, uint32_t sweep, double* u_prop,
+                        double* u_acc);
 
 /* Data -> spin mapping over the measured values; returns 2 on < 2 measured sites or zmax == zmin. */
 int mpro_map(int N, const double* z, const uint8_t* mask, double* phi, double* zmin, double* zmax);

@@ -477,6 +477,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.invT = 1.0 / T;
     a.qf = (float)h->opt.q;
     a.invTf = (float)(1.0 / T);
+    a.nl2eTf = -1.4426950408889634f * a.invTf;   // FP32 product, as the batched kernels form it
     a.epart = h->part;
     a.err = dev_err(h);
     a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds

@@ -256,6 +256,7 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
     a.invT = 0.0;        // the FP32 tile uses qf and invTf only
     a.qf = A->qf;
     a.invTf = __ldcg(&P.d.invTf);
+    a.nl2eTf = -1.4426950408889634f * a.invTf;
     if constexpr (SCHED) {
         a.ph = *ks;
         const uint64_t m = (uint64_t)0xCD9E8D57u * a.sweep;

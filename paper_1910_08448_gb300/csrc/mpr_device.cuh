@@ -36,14 +36,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 // Random stream of a site pair: counter (x >> 2, y, sweep, problem << 8 | tag << 1 | colour),
 // key = seed. The pair's first site (half-lattice column j even) takes words (x, y), the second
 // (j odd) takes (z, w); the first word of a site drives its proposal or initial angle, the
-// second its acceptance test.
+// second its acceptance test. (The initial angles of every setup and the Metropolis moves of
+// the FP64-function setting use this layout; the FP32-function Metropolis moves call the same
+// function with counter (g, h, sweep, problem << 8 | sub << 2 | colour) for a group of eight
+// sites, see mpr_tile_f32.cuh.)
 enum : uint32_t { kTagMetropolis = 0, kTagInit = 1 };
 
 __device__ __forceinline__ uint4 pair_words(uint32_t jpair, uint32_t y, uint32_t sweep,
                                             uint32_t problem, uint32_t tag, uint32_t colour,
-                                            uint32_t seed_lo, uint32_t seed_hi)
+                                            uint32_t seed_lo, uint32_t seed_hi, uint32_t sub = 0u)
 {
-    return philox4x32_10(make_uint4(jpair, y, sweep, (problem << 8) | (tag << 1) | colour),
+    return philox4x32_10(make_uint4(jpair, y, sweep,
+                                    (problem << 8) | (sub << 2) | (tag << 1) | colour),
                          seed_lo, seed_hi);
 }
 
@@ -75,10 +79,11 @@ __host__ __device__ inline PhiloxSched philox_sched(uint32_t sweep, uint32_t pro
     return s;
 }
 
-__device__ __forceinline__ uint4 pair_words(uint32_t jpair, uint32_t y, const PhiloxSched& s)
+__device__ __forceinline__ uint4 pair_words(uint32_t jpair, uint32_t y, const PhiloxSched& s,
+                                            uint32_t sub = 0u)
 {
     const uint64_t p0 = (uint64_t)0xD2511F53u * jpair;
-    uint4 x = make_uint4(s.a ^ y, s.b, (uint32_t)(p0 >> 32) ^ s.c, (uint32_t)p0);
+    uint4 x = make_uint4(s.a ^ y, s.b, (uint32_t)(p0 >> 32) ^ s.c ^ (sub << 2), (uint32_t)p0);
 #pragma unroll
     for (int r = 1; r < 10; ++r) {
         const uint64_t q0 = (uint64_t)0xD2511F53u * x.x;
@@ -100,6 +105,11 @@ __device__ __forceinline__ float one_plus_uniform_f(uint32_t w)
 // Exactly (w >> 9) * 2^-23, no conversion op. c * uniform_f(w) == fmaf(c, one_plus_uniform_f(w), -c)
 // bit for bit, since both round the same exact product once.
 __device__ __forceinline__ float uniform_f(uint32_t w) { return one_plus_uniform_f(w) - 1.0f; }
+// 1 + m * 2^-23 for the low 23 bits m of v, exactly (one logic op).
+__device__ __forceinline__ float one_plus_low23_f(uint32_t v)
+{
+    return __uint_as_float((v & 0x007FFFFFu) | 0x3f800000u);
+}
 
 // ---------------------------------------------------------------------------------------------
 // Storage conversions

@@ -62,6 +62,7 @@ struct SweepArgs {
     uint32_t seed_lo, seed_hi, sweep, problem;
     double q, T, invT;
     float qf, invTf;           // the same in FP32 for the FP32-function kernel (no FP64 on device)
+    float nl2eTf;              // -log2(e) * invTf as one FP32 product: exp(-dE/T) = 2^(dE * nl2eTf)
     int* err;                  // device error word (MPR_ERR_DEVICE_TIMEOUT) or NULL
     long long wait_ns;         // limit of one device-side wait (TMA kernel)
     int stall_test;            // test hook: block 0 of the TMA kernel issues no copy for its

@@ -27,25 +27,28 @@ constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 // tile of the same height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the
 // batched kernels do: the energy partials, and so the energies, stay bit-identical between the
 // two paths.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, bool W1>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, int QM>
 __device__ __forceinline__ void block_tile(const SweepArgs& a, int b, TileSmem<R>& sm, void* eslot)
 {
     const int ntx = (a.Lxh + kTJ - 1) / kTJ;
     const int tx = b % ntx, ty = b / ntx;
     const int rem = a.Lxh - tx * kTJ;
     if (tx == ntx - 1 && rem <= 32)
-        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32, W1>(
+        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32, QM>(
             a, 4 * tx, ty, *reinterpret_cast<TileSmem<R / 4, 32>*>(&sm), eslot);
     else if (tx == ntx - 1 && rem <= 64)
-        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64, W1>(
+        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64, QM>(
             a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
     else
-        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, W1>(a, tx, ty, sm, eslot);
+        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, QM>(a, tx, ty, sm, eslot);
 }
 
+#ifndef MPR_X_LB
+#define MPR_X_LB 4
+#endif
 template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
-                                       : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
+                                       : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : MPR_X_LB))
     sweep_f32_kernel(const SweepArgs a)
 {
     static_assert(R % 4 == 0, "the 64- and 32-column tail tiles have R / 2 and R / 4 rows per thread");
@@ -55,16 +58,16 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     void* eslot = nullptr;
     if (MEASURE)
         eslot = static_cast<char*>(a.epart) + (size_t)b * ((a.flags & kEnergyF32) ? 4 : 8);
-    // the plain pass (most passes) with 16-bit spins has a copy for q <= 1/2 (the default) with
-    // one angle wrap; the branch is uniform over the grid (with FP32 spins the second copy would
-    // spill registers)
+    // the plain pass (most passes) with 16-bit spins has a copy for q = 1/2 (the paper's value
+    // and the default) with q a compile-time constant; the branch is uniform over the grid (with
+    // FP32 spins the second copy would spill registers)
     if constexpr (!MEASURE && SAMPLE == 0 && sizeof(S) == 2) {
-        if (a.qf <= 0.5f) {
-            block_tile<S, R, MEASURE, SAMPLE, PROP, true>(a, b, sm, eslot);
+        if (a.qf == 0.5f) {
+            block_tile<S, R, MEASURE, SAMPLE, PROP, 2>(a, b, sm, eslot);
             return;
         }
     }
-    block_tile<S, R, MEASURE, SAMPLE, PROP, false>(a, b, sm, eslot);
+    block_tile<S, R, MEASURE, SAMPLE, PROP, 0>(a, b, sm, eslot);
 }
 
 // Launched as a programmatic dependent launch: while the previous pass's last blocks finish, this

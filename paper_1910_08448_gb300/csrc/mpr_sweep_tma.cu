@@ -130,14 +130,17 @@ __global__ void __launch_bounds__(256, 3)
         double e_d = 0.0;   // unused: no energy in plain passes
         float e_f = 0.0f;
         int n_acc = 0;      // unused: uniform proposals only
+        GroupCarry gc{0u, 0u, 0u, 0u};
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int ly = warp * R + row_of<R>(i, a.colour);
             const int y = y0 + ly;
+            if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + warp * R + row_of<R>(i - 1, a.colour) >= a.Ly)
+                group_carry_only<true>(a, y, jb, gc);
             if (y < a.Ly)
                 update_row_i<S, R, false, 0, true, false, false>(i, a, y, ly, jb, lj, mine[i],
                                                                  bits[i], sm.t, e_d, e_f, 0.0f,
-                                                                 n_acc);
+                                                                 n_acc, gc);
         }
         if (leader && tn < ntiles) await(it + 1);
         __syncthreads();   // the unit vectors' readers are done; sm.ok is current

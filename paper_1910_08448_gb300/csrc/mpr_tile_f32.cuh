@@ -70,6 +70,63 @@ __device__ __forceinline__ float atan2_doubled(float y, float x)
     return __uint_as_float(__float_as_uint(t2) ^ sgn);
 }
 
+// Two FP32 lanes per instruction (Blackwell's packed FP32 arithmetic: __ffma2_rn, __fadd2_rn,
+// __fmul2_rn). Each lane rounds exactly as the scalar FP32 operation would, so a pair of sites
+// computed in float2 gets the same bits as the two sites computed one by one; the kernel is
+// bound by instruction issue, and a packed instruction issues once for both sites.
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding (the product b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, splat(-1.0f), a); }
+
+// 1 / x on the MUFU (hand-written PTX: rcp.approx.ftz.f32)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// atan2_doubled of two sites at once: the same reduction and polynomial, the multiplies and the
+// polynomial in float2. The quotient is min * rcp(max) (approximate reciprocal on the MUFU); both
+// lanes NaN-propagate as the scalar version does when x = y = 0.
+template <bool SHORT>
+__device__ __forceinline__ float2 atan2_doubled2(float2 y, float2 x)
+{
+    const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
+    const float2 mx = make_float2(fmaxf(ax0, ay0), fmaxf(ax1, ay1));
+    const float2 mn = make_float2(fminf(ax0, ay0), fminf(ax1, ay1));
+    const float2 a = mul2(mn, make_float2(rcp_approx(mx.x), rcp_approx(mx.y)));
+    const float2 s = mul2(a, a);
+    float2 p;
+    if constexpr (SHORT) {
+        p = splat(-0.023438263684511185f);
+        p = fma2(p, s, splat(0.10529468208551407f));
+        p = fma2(p, s, splat(-0.23285295069217682f));
+        p = fma2(p, s, splat(0.38708075881004333f));
+        p = fma2(p, s, splat(-0.6652456521987915f));
+        p = fma2(p, s, splat(1.9999544620513916f));
+    } else {
+        p = splat(-0.008109131827950478f);
+        p = fma2(p, s, splat(0.04372590780258179f));
+        p = fma2(p, s, splat(-0.1118246391415596f));
+        p = fma2(p, s, splat(0.1928439438343048f));
+        p = fma2(p, s, splat(-0.2781725823879242f));
+        p = fma2(p, s, splat(0.3989313244819641f));
+        p = fma2(p, s, splat(-0.6665971875190735f));
+        p = fma2(p, s, splat(1.999998688697815f));
+    }
+    const float2 t2 = mul2(a, p);
+    const float2 u = sub2(splat(3.14159265358979324f), t2);
+    const float r0 = ay0 > ax0 ? u.x : t2.x, r1 = ay1 > ax1 ? u.y : t2.y;
+    const uint32_t g0 = (__float_as_uint(x.x) ^ __float_as_uint(y.x)) & 0x80000000u;
+    const uint32_t g1 = (__float_as_uint(x.y) ^ __float_as_uint(y.y)) & 0x80000000u;
+    return make_float2(__uint_as_float(__float_as_uint(r0) ^ g0),
+                       __uint_as_float(__float_as_uint(r1) ^ g1));
+}
+
 template <typename S> struct Raw4;
 template <> struct Raw4<__half> { using T = uint2; };
 template <> struct Raw4<__nv_bfloat16> { using T = uint2; };
@@ -142,12 +199,22 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
     const int lc = threadIdx.x % Lanes<TJ>::kPerRow;   // lane within the row
     const bool row_ok = !CHECK || (y >= 0 && y < a.Ly);
     float vc[4], vs[4];
+    if constexpr (!CHECK) {
+        // q * phi of the four entries as two float2 products
+        const float2 a01 = mul2(splat(q), make_float2(load_as<float>(st.s[0]), load_as<float>(st.s[1])));
+        const float2 a23 = mul2(splat(q), make_float2(load_as<float>(st.s[2]), load_as<float>(st.s[3])));
+        __sincosf(a01.x, &vs[0], &vc[0]);
+        __sincosf(a01.y, &vs[1], &vc[1]);
+        __sincosf(a23.x, &vs[2], &vc[2]);
+        __sincosf(a23.y, &vs[3], &vc[3]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        vc[k] = 0.0f;
-        vs[k] = 0.0f;
-        if (!CHECK || (row_ok && 2 * (jb + k) + ob < a.Lx))
-            __sincosf(q * load_as<float>(st.s[k]), &vs[k], &vc[k]);
+        for (int k = 0; k < 4; ++k) {
+            vc[k] = 0.0f;
+            vs[k] = 0.0f;
+            if (row_ok && 2 * (jb + k) + ob < a.Lx)
+                __sincosf(q * load_as<float>(st.s[k]), &vs[k], &vc[k]);
+        }
     }
     *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
     *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
@@ -211,6 +278,50 @@ template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, fl
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// Metropolis random numbers of the FP32-function setting. Every uniform has 23 bits, so three
+// Philox-4x32-10 calls (384 bits) serve a group of eight same-colour sites: the thread's four
+// half-lattice columns jb .. jb+3 (g = jb >> 2) in the two rows 2h, 2h + 1 (h = y >> 1); call
+// sub (0, 1, 2) has counter (g, h, sweep, problem << 8 | sub << 2 | colour). The group's first
+// row is the one with y + colour even (the thread visits it first, see row_of). In the first row
+// the site pair t uses call t like the two-site layout: sites 2t, 2t + 1 take the top 23 bits of
+// words (x, y) and (z, w) for proposal and acceptance. In the second row site i takes the top 23
+// bits of word i of call 2 for its proposal, and its acceptance from the calls' low bytes (which
+// no top-23-bit field touches): site i gets bytes 3i, 3i+1, 3i+2 of the twelve words' low bytes
+// in call order, 23 bits of them. GroupCarry holds the first row's low bytes for the second row.
+struct GroupCarry {
+    uint32_t a0, a1;   // second-row sites 0, 1: bytes (W0, W1, W2), (W3, W4, W5) low bytes
+    uint32_t p2;       // site 2: bytes W6, W7 (W8 comes from call 2)
+    uint32_t w3;       // call 0's last word until call 1 completes a1
+};
+
+template <bool SCHED>
+__device__ __forceinline__ uint4 group_call(const SweepArgs& a, uint32_t g, uint32_t h, uint32_t sub)
+{
+    if constexpr (SCHED)
+        return pair_words(g, h, a.ph, sub);
+    else
+        return pair_words(g, h, a.sweep, a.problem, kTagMetropolis, (uint32_t)a.colour, a.seed_lo,
+                          a.seed_hi, sub);
+}
+
+// the low bytes of (x, y) in bytes 0, 1 of the result
+__device__ __forceinline__ uint32_t low2(uint32_t x, uint32_t y) { return __byte_perm(x, y, 0x0040u); }
+// bytes 0, 1 of p and the low byte of z in bytes 0, 1, 2
+__device__ __forceinline__ uint32_t low3(uint32_t p, uint32_t z) { return __byte_perm(p, z, 0x0410u); }
+
+// The first row's low bytes, from its two calls (or from recomputed calls when that row lies
+// outside the lattice).
+__device__ __forceinline__ void carry_call0(GroupCarry& gc, const uint4& w)
+{
+    gc.a0 = low3(low2(w.x, w.y), w.z);
+    gc.w3 = w.w;
+}
+__device__ __forceinline__ void carry_call1(GroupCarry& gc, const uint4& w)
+{
+    gc.a1 = low3(low2(gc.w3, w.x), w.y);
+    gc.p2 = low2(w.z, w.w);
+}
+
 // Metropolis + over-relaxation of the thread's four columns jb .. jb+3 of tile row ly (lattice
 // row y < Ly) of colour a.colour, reading the staged neighbours in sm; pk holds the four stored
 // values (updated in place and written back as one vector), bits their frozen bits. SAMPLE: 0
@@ -220,20 +331,25 @@ template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, fl
 // (a kernel parameter) instead of the seed. OPAR: the row's column offset o = (y + colour) & 1
 // when the caller knows it at compile time (0 or 1), else -1. PROP: bounded proposals
 // f + pw (2u - 1), rejected outside [0, 2 pi); n_acc counts the accepted ones of updated sites.
-// W1: the caller knows q <= 1/2, so the reflected angle needs one 2 pi wrap, not two.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, bool W1,
-          int TJ>
+// QM: 0 any q; 1 the caller knows q <= 1/2, so the reflected angle needs one 2 pi wrap, not two;
+// 2 q = 1/2 (the paper's value) at compile time: q*phi of the accepted angle is the proposal's
+// or the old angle's product (both computed for the energy), and r/q is r + r (exact).
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, int QM,
+          int TJ, int ROW>
 __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
                                            Pack4<S>& pk, uint32_t bits, const TileSmem<R, TJ>& sm,
-                                           double& e_d, float& e_f, float pw, int& n_acc)
+                                           double& e_d, float& e_f, float pw, int& n_acc,
+                                           GroupCarry& gc)
 {
     const int c = a.colour;
     S* __restrict__ own = static_cast<S*>(a.own);
-    const float q = a.qf;
-    const float nl2e_invT = -1.4426950408889634f * a.invTf;   // exp(-dE/T) = 2^(dE * nl2e_invT)
+    constexpr bool QH = QM == 2;
+    const float q = QH ? 0.5f : a.qf;
+    // exp(-dE/T) = 2^(dE * nl2e): nl2e = -log2(e) * (1/T), the FP32 product formed by the caller
+    const float nl2e = a.nl2eTf;
     const float two_pi = kTwoPiF;
-    const float width = two_pi * q;
-    const float inv_q = 1.0f / q;
+    const float width = QH ? 3.14159265358979324f : two_pi * q;
+    const float inv_q = QH ? 2.0f : 1.0f / q;
     const int o = OPAR >= 0 ? OPAR : ((y + c) & 1);
     const size_t idx = (size_t)y * a.pitch + jb;
     // entries past the row's end carry frozen bits (padding), so the bit alone decides an update;
@@ -244,9 +360,10 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
         ex[k] = 2 * (jb + k) + o < a.Lx;
         upd[k] = !((bits >> k) & 1u);
     }
-    // local fields h = sum of the neighbours' unit vectors (left, right, up, down), all four sites
-    // first: the neighbour vectors are dead before the moves start
-    float hx[4], hy[4];
+    // local fields h = sum of the neighbours' unit vectors (left, right, up, down), sites 2t and
+    // 2t + 1 in lanes x and y of hx2[t], hy2[t]; all four sites first: the neighbour vectors are
+    // dead before the moves start. Order of the sums: ((left + right) + up) + down.
+    float2 hx2[2], hy2[2];
     {
         // up/down rows at the same columns, the middle row at columns j+o-1, j+o
         const float4 uc = *reinterpret_cast<const float4*>(&sm.cs[ly][4 + lj]);
@@ -260,108 +377,183 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
         // middle row values m[0..4] = columns j+o-1 .. j+o+3 (site k: left m[k], right m[k+1])
         const float mcv[5] = {o ? mc4.x : ec, o ? mc4.y : mc4.x, o ? mc4.z : mc4.y, o ? mc4.w : mc4.z, o ? ec : mc4.w};
         const float msv[5] = {o ? ms4.x : es, o ? ms4.y : ms4.x, o ? ms4.z : ms4.y, o ? ms4.w : ms4.z, o ? es : ms4.w};
-        const float ucv[4] = {uc.x, uc.y, uc.z, uc.w}, usv[4] = {us.x, us.y, us.z, us.w};
-        const float dcv[4] = {dc.x, dc.y, dc.z, dc.w}, dsv[4] = {ds.x, ds.y, ds.z, ds.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            hx[k] = ((mcv[k] + mcv[k + 1]) + ucv[k]) + dcv[k];
-            hy[k] = ((msv[k] + msv[k + 1]) + usv[k]) + dsv[k];
-        }
+        hx2[0] = add2(add2(make_float2(mcv[0] + mcv[1], mcv[1] + mcv[2]), make_float2(uc.x, uc.y)),
+                      make_float2(dc.x, dc.y));
+        hx2[1] = add2(add2(make_float2(mcv[2] + mcv[3], mcv[3] + mcv[4]), make_float2(uc.z, uc.w)),
+                      make_float2(dc.z, dc.w));
+        hy2[0] = add2(add2(make_float2(msv[0] + msv[1], msv[1] + msv[2]), make_float2(us.x, us.y)),
+                      make_float2(ds.x, ds.y));
+        hy2[1] = add2(add2(make_float2(msv[2] + msv[3], msv[3] + msv[4]), make_float2(us.z, us.w)),
+                      make_float2(ds.z, ds.w));
     }
-    uint4 w;
-    float fn_even = 0.0f;
     float ev[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // MEASURE: u_b . h_b of the row's sites
+    // Random numbers (see GroupCarry), whether or not the sites update: no branch per site.
+    // ROW 0: first row of the group; 1: second row (gc from the first); 2: the thread's only row
+    // of the group (odd rows per thread: the group's other row belongs to another thread), whose
+    // role follows from y + colour.
+    const uint32_t g = (uint32_t)(jb >> 2), h = (uint32_t)(y >> 1);
+    uint4 w2 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 wl0 = w2, wl1 = w2;
+    bool second = ROW == 1;
+    if constexpr (ROW == 2) {
+        second = ((y + c) & 1) != 0;
+        wl0 = group_call<SCHED>(a, g, h, 0u);
+        wl1 = group_call<SCHED>(a, g, h, 1u);
+        carry_call0(gc, wl0);
+        carry_call1(gc, wl1);
+    }
+    if constexpr (ROW != 0) w2 = group_call<SCHED>(a, g, h, 2u);
+    const uint32_t a2 = low3(gc.p2, w2.x), a3 = low3(low2(w2.y, w2.z), w2.w);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        // one Philox call per site pair, whether or not its sites update: no branch per site
-        if ((k & 1) == 0) {
-            const uint32_t jpair = (uint32_t)((jb >> 1) + (k >> 1));
-            if constexpr (SCHED)
-                w = pair_words(jpair, (uint32_t)y, a.ph);
-            else
-                w = pair_words(jpair, (uint32_t)y, a.sweep, a.problem, kTagMetropolis,
-                               (uint32_t)c, a.seed_lo, a.seed_hi);
-        }
-        const float hxk = hx[k], hyk = hy[k];
-        float f = load_as<float>(pk.s[k]);
+    for (int t = 0; t < 2; ++t) {
+        const int k0 = 2 * t, k1 = 2 * t + 1;   // the pair's sites (lanes x and y)
+        // 1 + u of the pair's proposal (op) and acceptance (oa) uniforms
+        float2 op, oa;
         {
-            // every site runs the move; frozen sites and padding discard the result below
-            const uint32_t wp = (k & 1) ? w.z : w.x;
-            const uint32_t wa = (k & 1) ? w.w : w.y;
-            const float u_acc = uniform_f(wa);
-            // Metropolis: uniform proposal fp = 2 pi u (or bounded: f + pw (2u - 1), inside
-            // [0, 2 pi) only), accept if dE <= 0 or u_acc < exp(-dE/T)
-            float fp;
-            bool inside = true;
-            if constexpr (PROP) {
-                fp = fmaf(2.0f * pw, uniform_f(wp), f - pw);
-                inside = fp >= 0.0f && fp < two_pi;
-            } else {
-                fp = fmaf(two_pi, one_plus_uniform_f(wp), -two_pi);
+            uint4 w;
+            if constexpr (ROW == 0) {
+                w = group_call<SCHED>(a, g, h, (uint32_t)t);
+                if (t == 0) carry_call0(gc, w); else carry_call1(gc, w);
+            } else if constexpr (ROW == 2) {
+                w = t == 0 ? wl0 : wl1;
             }
-            float s0, c0, sp, cp;
-            __sincosf(q * f, &s0, &c0);
-            __sincosf(q * fp, &sp, &cp);
-            // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
-            const float dE = hxk * (c0 - cp) + hyk * (s0 - sp);
-            const bool accept = inside && (dE <= 0.0f || u_acc < ex2_approx(dE * nl2e_invT));
-            if constexpr (PROP) n_acc += (accept && upd[k]) ? 1 : 0;
-            const float f1 = accept ? fp : f;
-            // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
-            // h = 0 gives NaN in atan2_doubled, every comparison below is false and the angle
-            // stays, as the move requires.
-            float r = atan2_doubled<sizeof(S) == 2>(hyk, hxk) - q * f1;   // in [-pi - 2 pi q, pi]
-            // r < 0 ? r + 2 pi : r, twice, on the FMA pipe: the saturated product is 1 for every
-            // negative normal r and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the
-            // rounding of a plain add. (A nonzero r is never subnormal: its two terms are 0 or at
-            // least ~1e-8 in magnitude.)
-            // (with q <= 1/2, r >= -2 pi and the first wrap already lands in [0, 2 pi); the second
-            // would add 0, so W1 drops it without changing a bit)
-            r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
-            if constexpr (!W1) r = fmaf(two_pi, __saturatef(r * -0x1.0p126f), r);
-            const float fn = r <= width ? r * inv_q : f1;
-            if constexpr (sizeof(S) == 2) {
-                // 16-bit storage: the pair's two results rounded by one conversion and merged into
-                // the pair's 32-bit word under the update mask
-                if ((k & 1) == 0) {
-                    fn_even = fn;
-                } else {
-                    const uint32_t m = (upd[k - 1] ? 0x0000FFFFu : 0u) | (upd[k] ? 0xFFFF0000u : 0u);
-                    const uint32_t packed = pack2<S>(fn_even, fn);
-                    if (k == 1) pk.v.x = (packed & m) | (pk.v.x & ~m);
-                    else pk.v.y = (packed & m) | (pk.v.y & ~m);
+            const float2 op_f = make_float2(one_plus_uniform_f(w.x), one_plus_uniform_f(w.z));
+            const float2 oa_f = make_float2(one_plus_uniform_f(w.y), one_plus_uniform_f(w.w));
+            const float2 op_s = t == 0 ? make_float2(one_plus_uniform_f(w2.x), one_plus_uniform_f(w2.y))
+                                       : make_float2(one_plus_uniform_f(w2.z), one_plus_uniform_f(w2.w));
+            const float2 oa_s = t == 0 ? make_float2(one_plus_low23_f(gc.a0), one_plus_low23_f(gc.a1))
+                                       : make_float2(one_plus_low23_f(a2), one_plus_low23_f(a3));
+            if constexpr (ROW == 0) {
+                op = op_f;
+                oa = oa_f;
+            } else if constexpr (ROW == 1) {
+                op = op_s;
+                oa = oa_s;
+            } else {
+                op = second ? op_s : op_f;
+                oa = second ? oa_s : oa_f;
+            }
+        }
+        const float2 hx = hx2[t], hy = hy2[t];
+        const float2 f = make_float2(load_as<float>(pk.s[k0]), load_as<float>(pk.s[k1]));
+        // every site runs the move; a frozen site (or padding) rejects both moves, so its result
+        // is its own value
+        // Metropolis: uniform proposal fp = 2 pi u (or bounded: f + pw (2u - 1), inside
+        // [0, 2 pi) only), accept if dE <= 0 or u_acc < exp(-dE/T). The first word of a site
+        // drives its proposal, the second its acceptance.
+        const float2 u_acc = add2(oa, splat(-1.0f));
+        float2 fp;
+        bool inside0 = true, inside1 = true;
+        if constexpr (PROP) {
+            const float2 u_p = add2(op, splat(-1.0f));
+            fp = fma2(splat(2.0f * pw), u_p, add2(f, splat(-pw)));
+            inside0 = (fp.x >= 0.0f) & (fp.x < two_pi);
+            inside1 = (fp.y >= 0.0f) & (fp.y < two_pi);
+        } else if constexpr (!QH) {
+            fp = fma2(splat(two_pi), op, splat(-two_pi));
+        }
+        // q * phi of the old angle and of the proposal. With q = 1/2 and uniform proposals,
+        // q * fp = pi * (1 + u) - pi rounded once, and fp = 2 * (q * fp) exactly: the same bits as
+        // fp = 2 pi (1 + u) - 2 pi rounded once, then halved.
+        const float2 qf = mul2(splat(q), f);
+        float2 qp;
+        if constexpr (QH && !PROP) {
+            qp = fma2(splat(3.14159265358979324f), op, splat(-3.14159265358979324f));
+            fp = add2(qp, qp);
+        } else {
+            qp = mul2(splat(q), fp);
+        }
+        float2 s0, c0, sp, cp;
+        __sincosf(qf.x, &s0.x, &c0.x);
+        __sincosf(qf.y, &s0.y, &c0.y);
+        __sincosf(qp.x, &sp.x, &cp.x);
+        __sincosf(qp.y, &sp.y, &cp.y);
+        // dE = E(fp) - E(f), E(phi) = -(hx cos q*phi + hy sin q*phi)
+        const float2 dE = fma2(hx, sub2(c0, cp), mul2(hy, sub2(s0, sp)));
+        const float2 ea = make_float2(dE.x * nl2e, dE.y * nl2e);
+        // both exponentials always (no branch per site); the decisions combine without
+        // short-circuit evaluation
+        const float e0 = ex2_approx(ea.x), e1 = ex2_approx(ea.y);
+        const bool acc0 = upd[k0] & inside0 & ((dE.x <= 0.0f) | (u_acc.x < e0));
+        const bool acc1 = upd[k1] & inside1 & ((dE.y <= 0.0f) | (u_acc.y < e1));
+        if constexpr (PROP) n_acc += (acc0 ? 1 : 0) + (acc1 ? 1 : 0);
+        const float2 f1 = make_float2(acc0 ? fp.x : f.x, acc1 ? fp.y : f.y);
+        // over-relaxation: reflect q*phi about arg(h); keep it if it lands in [0, 2*pi*q].
+        // h = 0 gives NaN in atan2_doubled2, every comparison below is false and the angle
+        // stays, as the move requires.
+        float2 r;   // in [-pi - 2 pi q, pi]
+        if constexpr (QH) {
+            const float2 qf1 = make_float2(acc0 ? qp.x : qf.x, acc1 ? qp.y : qf.y);   // q * f1, exact
+            r = sub2(atan2_doubled2<sizeof(S) == 2>(hy, hx), qf1);
+        } else {
+            r = fma2(splat(-q), f1, atan2_doubled2<sizeof(S) == 2>(hy, hx));
+        }
+        // r < 0 ? r + 2 pi : r, twice: the saturated product is 1 for every negative normal r
+        // and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the rounding of a plain
+        // add. (A nonzero r is never subnormal: its two terms are 0 or at least ~1e-8 in
+        // magnitude.) With q <= 1/2, r >= -2 pi and the first wrap already lands in [0, 2 pi);
+        // the second would add 0, so QM > 0 drops it without changing a bit.
+        r = fma2(splat(two_pi), make_float2(__saturatef(r.x * -0x1.0p126f),
+                                            __saturatef(r.y * -0x1.0p126f)), r);
+        if constexpr (QM == 0)
+            r = fma2(splat(two_pi), make_float2(__saturatef(r.x * -0x1.0p126f),
+                                                __saturatef(r.y * -0x1.0p126f)), r);
+        const float2 rq = QH ? add2(r, r) : mul2(r, splat(inv_q));
+        float2 fn = make_float2(upd[k0] & (r.x <= width) ? rq.x : f1.x,
+                                upd[k1] & (r.y <= width) ? rq.y : f1.y);
+        if constexpr (sizeof(S) == 2) {
+            // 16-bit storage: the pair's two results rounded by one paired conversion; a frozen
+            // site's own value converts back to its stored bits exactly
+            const uint32_t packed = pack2<S>(fn.x, fn.y);
+            if (t == 0) pk.v.x = packed; else pk.v.y = packed;
+            if (SAMPLE || MEASURE) {
+                Pack4<S> back;
+                back.v.x = packed;
+                fn = make_float2(load_as<float>(back.s[0]), load_as<float>(back.s[1]));
+            }
+        } else if constexpr (sizeof(S) == 4) {
+            pk.s[k0] = fn.x;   // exact for a frozen site
+            pk.s[k1] = fn.y;
+        } else {
+            // FP64 storage: a frozen site's FP64 value is not an FP32 value; keep it
+            if (upd[k0]) pk.s[k0] = store_from<S>(fn.x);
+            if (upd[k1]) pk.s[k1] = store_from<S>(fn.y);
+            fn = make_float2(load_as<float>(pk.s[k0]), load_as<float>(pk.s[k1]));
+        }
+        // the site's angle after the move, as stored (SAMPLE and MEASURE use it)
+        const float fs[2] = {fn.x, fn.y};
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int k = k0 + l;
+            if (SAMPLE == 1) {
+                if (upd[k]) a.acc[idx + k] += (double)fs[l];
+            } else if (SAMPLE == 2) {
+                if (upd[k]) {
+                    // Kahan: hi carries the sum, lo the (negated) lost low-order part
+                    const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
+                    const float yv = fs[l] - lo;
+                    const float tt = hi + yv;
+                    a.acc_lo[idx + k] = (tt - hi) - yv;
+                    a.acc_hi[idx + k] = tt;
                 }
-                if (SAMPLE || MEASURE) f = upd[k] ? load_as<float>(store_from<S>(fn)) : f;
-            } else {
-                const S stored = store_from<S>(fn);
-                pk.s[k] = upd[k] ? stored : pk.s[k];
-                f = upd[k] ? load_as<float>(stored) : f;
+            } else if (SAMPLE == 3) {
+                // FP16 spins, FP64 sums: f is an FP16 value, an integer multiple of 2^-24 below
+                // 2^3, so f * 2^24 converts to an int exactly and 16 of them fit an int32; the
+                // handle folds the partial into the FP64 sum, where every add is exact (the sum
+                // stays a multiple of 2^-24 below 2^29): the same bits as adding f itself, with a
+                // 4-byte read and write per sample instead of 8-byte ones
+                if (upd[k]) a.part32[idx + k] += __float2int_rn(fs[l] * 16777216.0f);
             }
         }
-        if (SAMPLE == 1) {
-            if (upd[k]) a.acc[idx + k] += (double)f;
-        } else if (SAMPLE == 2) {
-            if (upd[k]) {
-                // Kahan: hi carries the sum, lo the (negated) lost low-order part
-                const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
-                const float yv = f - lo;
-                const float tt = hi + yv;
-                a.acc_lo[idx + k] = (tt - hi) - yv;
-                a.acc_hi[idx + k] = tt;
-            }
-        } else if (SAMPLE == 3) {
-            // FP16 spins, FP64 sums: f is an FP16 value, an integer multiple of 2^-24 below
-            // 2^3, so f * 2^24 converts to an int exactly and 16 of them fit an int32; the
-            // handle folds the partial into the FP64 sum, where every add is exact (the sum stays
-            // a multiple of 2^-24 below 2^29): the same bits as adding f itself, with a 4-byte
-            // read and write per sample instead of 8-byte ones
-            if (upd[k]) a.part32[idx + k] += __float2int_rn(f * 16777216.0f);
-        }
-        if (MEASURE && ex[k]) {
+        if (MEASURE) {
             // every bond joins a red and a black site: sum over black sites of u_b . h_b
-            float sn, cs;
-            __sincosf(q * f, &sn, &cs);
-            ev[k] = cs * hxk + sn * hyk;
+            const float2 qn = mul2(splat(q), fn);
+            float2 sn, cs;
+            __sincosf(qn.x, &sn.x, &cs.x);
+            __sincosf(qn.y, &sn.y, &cs.y);
+            const float2 e2 = fma2(cs, hx, mul2(sn, hy));
+            ev[k0] = ex[k0] ? e2.x : 0.0f;
+            ev[k1] = ex[k1] ? e2.y : 0.0f;
         }
     }
     if (MEASURE) {
@@ -412,23 +604,35 @@ template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R
 
 // update_row of the i-th row in the order row_of(), with o fixed at compile time for even R (the
 // branch on i & 1 disappears when the caller's loop over i is unrolled).
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, bool W1, int TJ>
+// With even R, i even is the first row of its Philox group (see GroupCarry) and i odd the second;
+// with odd R each row computes its group's three calls itself.
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, int QM, int TJ>
 __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
                                              int lj, Pack4<S>& pk, uint32_t bits,
                                              const TileSmem<R, TJ>& sm, double& e_d, float& e_f,
-                                             float pw, int& n_acc)
+                                             float pw, int& n_acc, GroupCarry& gc)
 {
     if constexpr (R % 2 == 0) {
         if (i & 1)
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d,
-                                                              e_f, pw, n_acc);
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP, QM, TJ, 1>(a, y, ly, jb, lj, pk, bits,
+                                                                       sm, e_d, e_f, pw, n_acc, gc);
         else
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d,
-                                                              e_f, pw, n_acc);
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP, QM, TJ, 0>(a, y, ly, jb, lj, pk, bits,
+                                                                       sm, e_d, e_f, pw, n_acc, gc);
     } else {
-        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP, W1>(a, y, ly, jb, lj, pk, bits, sm, e_d, e_f,
-                                                           pw, n_acc);
+        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP, QM, TJ, 2>(a, y, ly, jb, lj, pk, bits, sm,
+                                                                    e_d, e_f, pw, n_acc, gc);
     }
+}
+
+// A thread's first row of a Philox group lies outside the lattice (odd Ly) while its second row
+// exists: the second row still needs the first row's low bytes.
+template <bool SCHED>
+__device__ __forceinline__ void group_carry_only(const SweepArgs& a, int y, int jb, GroupCarry& gc)
+{
+    const uint32_t g = (uint32_t)(jb >> 2), h = (uint32_t)(y >> 1);
+    carry_call0(gc, group_call<SCHED>(a, g, h, 0u));
+    carry_call1(gc, group_call<SCHED>(a, g, h, 1u));
 }
 
 // Adds the block's accepted bounded proposals to *counter: warp sums, then one atomic per block
@@ -459,9 +663,9 @@ __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* co
 // Everything the previous pass may write (the other colour, accumulators, energy partials) is
 // touched only after the wait.
 // PROP: bounded proposals of half-width *a.width; accepted ones counted into *a.accepted.
-// W1: the caller has checked q <= 1/2 (one 2 pi wrap of the reflected angle suffices).
+// QM: 1 the caller has checked q <= 1/2 (one 2 pi wrap of the reflected angle suffices); 2 q = 1/2.
 template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false,
-          bool PROP = false, int TJ = kTJ, bool W1 = false>
+          bool PROP = false, int TJ = kTJ, int QM = 0>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
@@ -485,7 +689,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const int y = y0 + row0 + row_of<R>(i, c);
         bits[i] = 0xFu;
         if (y < a.Ly) {
+#ifndef MPR_X_LAZY
             load4(own + (size_t)y * a.pitch + jb, mine[i]);
+#else
+            if (i < MPR_X_LAZY) load4(own + (size_t)y * a.pitch + jb, mine[i]);
+#endif
             bits[i] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
         }
     }
@@ -498,21 +706,31 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
     // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
     // lies inside the lattice (nearly all) skip the per-entry bounds checks.
     const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + TJ) + 1 < a.Lx;
-    if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
-    else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, a.qf, sm);
+    const float qs = QM == 2 ? 0.5f : a.qf;
+    if (interior) stage<S, R, false>(a, other, y0, j0, jb, lj, cb, qs, sm);
+    else stage<S, R, true>(a, other, y0, j0, jb, lj, cb, qs, sm);
     __syncthreads();
 
     double e_d = 0.0;
     float e_f = 0.0f;
     const float pw = PROP ? (float)*a.width : 0.0f;   // written before this pass (stream order)
     int n_acc = 0;
+    GroupCarry gc{0u, 0u, 0u, 0u};
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int ly = row0 + row_of<R>(i, c);
         const int y = y0 + ly;
+        if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + row0 + row_of<R>(i - 1, c) >= a.Ly)
+            group_carry_only<SCHED>(a, y, jb, gc);
+#ifdef MPR_X_LAZY
+        if (i + MPR_X_LAZY < R) {   // the row MPR_X_LAZY ahead, while this one updates
+            const int yn = y0 + row0 + row_of<R>(i + MPR_X_LAZY, c);
+            if (yn < a.Ly) load4(own + (size_t)yn * a.pitch + jb, mine[i + MPR_X_LAZY]);
+        }
+#endif
         if (y < a.Ly)
-            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, W1>(i, a, y, ly, jb, lj, mine[i], bits[i],
-                                                             sm, e_d, e_f, pw, n_acc);
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM>(i, a, y, ly, jb, lj, mine[i], bits[i],
+                                                             sm, e_d, e_f, pw, n_acc, gc);
     }
     if (PROP && a.accepted) count_accepted(n_acc, a.accepted);
     if (MEASURE) tile_energy(a, e_d, e_f, sm, eslot);

@@ -111,7 +111,7 @@ def _exact_moments(Lx, Ly, frozen, T, n=48):
     return e, means
 
 
-def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000, width=0.0):
+def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000, width=0.0, ubits=32):
     mask = np.zeros((Ly, Lx), np.uint8)
     phi = np.zeros((Ly, Lx))
     for s, a in frozen.items():
@@ -119,7 +119,7 @@ def _mc_moments(orc, Lx, Ly, frozen, T, chains=16, equil=500, nsweeps=12000, wid
         phi.flat[s] = a
     es, ms = [], []
     for c in range(chains):
-        o = orc.Oracle(Lx, Ly, seed=1000 + c, width=width)
+        o = orc.Oracle(Lx, Ly, seed=1000 + c, width=width, ubits=ubits)
         p = o.init(phi, mask)
         p, _, _ = o.run(p, mask, T, 0, equil)
         p, acc, e = o.run(p, mask, T, equil, nsweeps, acc=np.zeros_like(p), energies=True)
@@ -140,12 +140,16 @@ CASES = [
 ]
 
 
+# ubits = 23: the FP32 setting's 23-bit uniforms, three Philox calls per group of eight sites
+# (on 3 x 3 lattices both rows of a group occur, so both the first-row and the byte-assembled
+# second-row acceptance uniforms drive the chain)
+@pytest.mark.parametrize("ubits", [32, 23])
 @pytest.mark.parametrize("Lx,Ly,frozen,T", CASES)
-def test_mc_matches_brute_force_gibbs(orc, Lx, Ly, frozen, T):
+def test_mc_matches_brute_force_gibbs(orc, Lx, Ly, frozen, T, ubits):
     e_ex, m_ex = _exact_moments(Lx, Ly, frozen, T)
     e_ex2, _ = _exact_moments(Lx, Ly, frozen, T, n=64 if len(frozen) < Lx * Ly - 1 else 128)
     assert abs(e_ex - e_ex2) < 1e-9           # quadrature converged
-    e_mc, e_se, m_mc, m_se = _mc_moments(orc, Lx, Ly, frozen, T)
+    e_mc, e_se, m_mc, m_se = _mc_moments(orc, Lx, Ly, frozen, T, ubits=ubits)
     assert abs(e_mc - e_ex) < 4.5 * e_se + 1e-4, (e_mc, e_ex, e_se)
     for s, v in m_ex.items():
         y, x = divmod(s, Lx)

@@ -103,6 +103,71 @@ def test_philox4x32_uniform_and_avalanche(orc):
     assert abs(np.mean(flips) / 128 - 0.5) < 0.02
 
 
+def _group_uniforms(orc, o, g, h, sweep, colour):
+    """The 16 Metropolis uniforms (8 sites x proposal, acceptance) of the FP32 group g (four
+    half-lattice columns) in rows 2h, 2h + 1 of the given colour."""
+    out = []
+    for y in (2 * h, 2 * h + 1):
+        for i in range(4):
+            j = 4 * g + i
+            x = 2 * j + ((y + colour) & 1)
+            out.extend(o.site_uniforms(x, y, sweep))
+    return out
+
+
+def test_fp32_group_uniforms_uniform_and_independent(orc):
+    # The FP32 setting draws 16 uniforms of 23 bits from three Philox calls per group of eight
+    # sites. Each of the 16 slots must be uniform on [0, 1) (chi-square on 64 bins), every pair
+    # of slots uncorrelated, and every pair of their 368 bits independent: a slot that reused
+    # bits of another (a wrong word or byte, at any bit position) fails the last check.
+    from scipy import stats
+
+    o = orc.Oracle(64, 64, seed=0x5EED1234ABCD, ubits=23)
+    rows = []
+    for sweep in range(32):
+        for colour in (0, 1):
+            for h in range(16):
+                for g in range(4):
+                    rows.append(_group_uniforms(orc, o, g, h, sweep, colour))
+    u = np.array(rows)                        # (4096, 16)
+    n = u.shape[0]
+    assert np.all((u >= 0.0) & (u < 1.0))
+    assert np.all(u * 2**23 == np.floor(u * 2**23))   # 23-bit uniforms
+    for k in range(16):
+        counts = np.bincount((u[:, k] * 64).astype(int), minlength=64)
+        chi2 = ((counts - n / 64) ** 2 / (n / 64)).sum()
+        assert stats.chi2.sf(chi2, 63) > 1e-5, k
+    r = np.corrcoef(u.T)
+    off = r[~np.eye(16, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / math.sqrt(n), np.max(np.abs(off))
+    # bit level: the 16 x 23 = 368 bits of a group are pairwise independent fair bits. Two
+    # uniforms fed from the same source bit (a byte or word used twice, at any position) agree
+    # on that bit pair every time; independent bits agree half the time, with sd 0.5/sqrt(n) =
+    # 0.0078 here: over the 67 528 pairs the largest deviation of independent bits is about
+    # 4.9 sd, a shared bit 64 sd. Bound: 7 sd.
+    m = (u * 2**23).astype(np.int64)
+    bits = ((m[:, :, None] >> np.arange(23)) & 1).reshape(n, 16 * 23).astype(np.float64)
+    sd = 0.5 / math.sqrt(n)
+    assert np.max(np.abs(bits.mean(0) - 0.5)) < 6 * sd
+    agree = (bits.T @ bits + (1 - bits).T @ (1 - bits)) / n
+    off = agree[np.triu_indices(16 * 23, 1)]
+    assert np.max(np.abs(off - 0.5)) < 7 * sd, np.max(np.abs(off - 0.5)) / sd
+
+
+def test_fp32_group_streams_distinct(orc):
+    # every site of a 16 x 8 lattice, both colours' sites, two sweeps and two problems: all
+    # uniforms distinct (23-bit values: ~2e3 draws collide with probability ~2e-1 per pair set,
+    # so compare the (proposal, acceptance) pairs, 46 bits)
+    seen = set()
+    for problem in (0, 1):
+        o = orc.Oracle(16, 8, seed=42, problem=problem, ubits=23)
+        for sweep in (0, 1):
+            for y in range(8):
+                for x in range(16):
+                    seen.add(o.site_uniforms(x, y, sweep))
+    assert len(seen) == 2 * 2 * 16 * 8
+
+
 def test_site_words_distinct_streams(orc):
     o = orc.Oracle(9, 7, seed=42)
     seen = set()
