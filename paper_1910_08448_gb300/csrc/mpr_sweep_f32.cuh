@@ -43,12 +43,9 @@ __device__ __forceinline__ void block_tile(const SweepArgs& a, int b, TileSmem<R
         sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, QM>(a, tx, ty, sm, eslot);
 }
 
-#ifndef MPR_X_LB
-#define MPR_X_LB 4
-#endif
 template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
-                                       : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : MPR_X_LB))
+                                       : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
     sweep_f32_kernel(const SweepArgs a)
 {
     static_assert(R % 4 == 0, "the 64- and 32-column tail tiles have R / 2 and R / 4 rows per thread");

@@ -689,11 +689,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const int y = y0 + row0 + row_of<R>(i, c);
         bits[i] = 0xFu;
         if (y < a.Ly) {
-#ifndef MPR_X_LAZY
             load4(own + (size_t)y * a.pitch + jb, mine[i]);
-#else
-            if (i < MPR_X_LAZY) load4(own + (size_t)y * a.pitch + jb, mine[i]);
-#endif
             bits[i] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
         }
     }
@@ -722,12 +718,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const int y = y0 + ly;
         if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + row0 + row_of<R>(i - 1, c) >= a.Ly)
             group_carry_only<SCHED>(a, y, jb, gc);
-#ifdef MPR_X_LAZY
-        if (i + MPR_X_LAZY < R) {   // the row MPR_X_LAZY ahead, while this one updates
-            const int yn = y0 + row0 + row_of<R>(i + MPR_X_LAZY, c);
-            if (yn < a.Ly) load4(own + (size_t)yn * a.pitch + jb, mine[i + MPR_X_LAZY]);
-        }
-#endif
         if (y < a.Ly)
             update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM>(i, a, y, ly, jb, lj, mine[i], bits[i],
                                                              sm, e_d, e_f, pw, n_acc, gc);
