@@ -121,10 +121,9 @@ __device__ __forceinline__ float2 atan2_doubled2(float2 y, float2 x)
     const float2 t2 = mul2(a, p);
     const float2 u = sub2(splat(3.14159265358979324f), t2);
     const float r0 = ay0 > ax0 ? u.x : t2.x, r1 = ay1 > ax1 ? u.y : t2.y;
-    const uint32_t g0 = (__float_as_uint(x.x) ^ __float_as_uint(y.x)) & 0x80000000u;
-    const uint32_t g1 = (__float_as_uint(x.y) ^ __float_as_uint(y.y)) & 0x80000000u;
-    return make_float2(__uint_as_float(__float_as_uint(r0) ^ g0),
-                       __uint_as_float(__float_as_uint(r1) ^ g1));
+    // the sign of x*y (a product that underflows keeps its sign; r0, r1 >= 0 or NaN)
+    const float2 xy = mul2(x, y);
+    return make_float2(copysignf(r0, xy.x), copysignf(r1, xy.y));
 }
 
 template <typename S> struct Raw4;
@@ -188,10 +187,11 @@ __device__ __forceinline__ float ex2_approx(float x)
 }
 
 // Converts one staged row r (tile row y = y0 - 1 + r, parity ob of its columns) of the other
-// colour to unit vectors (cos q*phi, sin q*phi) in sm: the thread's four columns from st, the halo
-// column j0 - 1 (first lane of the row) or j0 + TJ (second lane) from halo. Entries outside the
-// lattice become (0, 0) (open boundaries); CHECK = false when the caller knows every entry exists.
-template <typename S, int R, bool CHECK, int TJ>
+// colour to unit vectors (cos q*phi, sin q*phi) in sm: the thread's four columns from st and, with
+// HALO, the halo column j0 - 1 (first lane of the row) or j0 + TJ (second lane) from halo. Entries
+// outside the lattice become (0, 0) (open boundaries); CHECK = false when the caller knows every
+// entry exists.
+template <typename S, int R, bool CHECK, int TJ, bool HALO = true>
 __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j0, int jb, int lj,
                                          int ob, float q, const Pack4<S>& st, S halo,
                                          TileSmem<R, TJ>& sm)
@@ -218,7 +218,7 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
     }
     *reinterpret_cast<float4*>(&sm.cs[r][4 + lj]) = make_float4(vc[0], vc[1], vc[2], vc[3]);
     *reinterpret_cast<float4*>(&sm.sn[r][4 + lj]) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-    if (lc < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index TJ + 4)
+    if (HALO && lc < 2) {   // halo columns j0 - 1 (index 3) and j0 + TJ (index TJ + 4)
         const int j = lc == 0 ? j0 - 1 : j0 + TJ;
         const int cc = lc == 0 ? 3 : TJ + 4;
         float hc = 0.0f, hs = 0.0f;
@@ -230,7 +230,9 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
 }
 
 // Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile from global
-// memory as unit vectors. All loads are issued before the sin/cos work.
+// memory as unit vectors. All loads are issued before the sin/cos work. The 2 (TY + 2) halo
+// entries (columns j0 - 1 and j0 + TJ) go to the block's first threads, one entry each, so no
+// warp runs a halo branch with two of its lanes.
 template <typename S, int R, bool CHECK, int TJ>
 __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ other, int y0,
                                       int j0, int jb, int lj, int cb, float q, TileSmem<R, TJ>& sm)
@@ -238,29 +240,39 @@ __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ 
     constexpr int TY = tile_rows<R, TJ>();
     constexpr int HW = Lanes<TJ>::kRows;
     constexpr int NR = (TY + 2 + kWarps * HW - 1) / (kWarps * HW);   // staged rows per thread
+    constexpr int NH = 2 * (TY + 2);                                  // halo entries
+    static_assert(NH <= 32 * kWarps, "one halo entry per thread");
     const int warp = threadIdx.y;
-    const int lc = threadIdx.x % Lanes<TJ>::kPerRow, lr = threadIdx.x / Lanes<TJ>::kPerRow;
+    const int lr = threadIdx.x / Lanes<TJ>::kPerRow;
+    const int tid = warp * 32 + threadIdx.x;
     Pack4<S> st[NR];
-    S halo[NR];
+    // this thread's halo entry: row hr = tid / 2, column j0 - 1 (tid even) or j0 + TJ (odd)
+    const int hr = tid >> 1, hj = (tid & 1) ? j0 + TJ : j0 - 1;
+    const int hy = y0 - 1 + hr;
+    const bool hok = tid < NH && (!CHECK || (hy >= 0 && hy < a.Ly && hj >= 0 &&
+                                             2 * hj + ((hy + cb) & 1) < a.Lx));
+    S hv{};
+    if (hok) hv = other[(size_t)hy * a.pitch + hj];
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int r = (warp + i * kWarps) * HW + lr;
         const int y = y0 - 1 + r;
-        if (r < TY + 2 && (!CHECK || (y >= 0 && y < a.Ly))) {
+        if (r < TY + 2 && (!CHECK || (y >= 0 && y < a.Ly)))
             load4(other + (size_t)y * a.pitch + jb, st[i]);
-            if (lc < 2) {
-                const int j = lc == 0 ? j0 - 1 : j0 + TJ;
-                if (!CHECK || (j >= 0 && 2 * j + ((y + cb) & 1) < a.Lx))
-                    halo[i] = other[(size_t)y * a.pitch + j];
-            }
-        }
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int r = (warp + i * kWarps) * HW + lr;
         if (r >= TY + 2) break;
         const int y = y0 - 1 + r;
-        unit_row<S, R, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st[i], halo[i], sm);
+        unit_row<S, R, CHECK, TJ, false>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st[i], S{}, sm);
+    }
+    if (tid < NH) {
+        float hc = 0.0f, hs = 0.0f;
+        if (hok) __sincosf(q * load_as<float>(hv), &hs, &hc);
+        const int cc = (tid & 1) ? TJ + 4 : 3;
+        sm.cs[hr][cc] = hc;
+        sm.sn[hr][cc] = hs;
     }
 }
 
