@@ -803,7 +803,7 @@ def main():
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if args.setup[2] == "D" else "f32",
+            "dtype": {"D": "f64", "S": "f32", "H": "f16+f32"}[args.setup[2]],
             "data": "synthetic", "config": config,
             "roofline": res["roof"], "cpu_baseline": cpu, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"],

@@ -50,8 +50,14 @@ typedef enum {
 /* Spin storage X_S (Sec. 2: DP or SP spin variables; 16-bit storage is the future work of Sec. 3). */
 typedef enum { MPR_STORE_F64 = 0, MPR_STORE_F32 = 1, MPR_STORE_F16 = 2, MPR_STORE_BF16 = 3 } mpr_store;
 /* Energy X_E and function X_F precision (Sec. 2): D = FP64, S = FP32 (functions: hardware
- * intrinsics __sinf/__cosf/__expf, as the paper uses for all SP function evaluations). */
-typedef enum { MPR_PREC_D = 0, MPR_PREC_S = 1 } mpr_prec;
+ * intrinsics __sinf/__cosf/__expf, as the paper uses for all SP function evaluations).
+ * H (functions only, FP16 spin storage only; FP16 arithmetic is the paper's future work, Sec. 3):
+ * as S, except that the over-relaxation's doubled field angle is computed in FP16 (half2)
+ * arithmetic from the FP32 field rounded to FP16 (error at most about 3.4e-3 rad on the doubled
+ * angle: 2.4e-3 from the FP16 polynomial and result, 1e-3 from the rounded components), so an
+ * over-relaxed angle moves by up to about 7e-3 rad more than with S; the Metropolis energy
+ * difference, the acceptance test and the angle wraps stay FP32. Uniform proposals only. */
+typedef enum { MPR_PREC_D = 0, MPR_PREC_S = 1, MPR_PREC_H = 2 } mpr_prec;
 /* Running sums of the sampled angles: FP64, or FP32 with Kahan compensation. */
 typedef enum { MPR_ACC_F64 = 0, MPR_ACC_KAHAN_F32 = 1 } mpr_acc;
 

@@ -6,7 +6,8 @@ is no CPU fallback: if the library has not been built, every call raises.
 
 Precision setups are named by the paper's three axes X_S X_E X_F (Sec. 2): spin storage, energy,
 functions; D = FP64, S = FP32 (functions: hardware intrinsics); for storage also H = FP16 and
-B = BF16. E.g. "DDD" (all FP64), "SDS" (FP32 spins, FP64 energy, FP32 intrinsics), "HDS".
+B = BF16; for functions also H = FP16 arithmetic where safe (FP16 spins only). E.g. "DDD" (all
+FP64), "SDS" (FP32 spins, FP64 energy, FP32 intrinsics), "HDS", "HDH".
 """
 from __future__ import annotations
 
@@ -31,6 +32,7 @@ MPR_ERR_STATE = 8
 
 STORE = {"D": 0, "S": 1, "H": 2, "B": 3}
 PREC = {"D": 0, "S": 1}
+FUNC = {"D": 0, "S": 1, "H": 2}   # X_F also has H: FP16 arithmetic where safe (FP16 spins only)
 ACC = {"f64": 0, "kahan": 1}
 
 
@@ -212,10 +214,10 @@ def mpr_trim_memory():
 
 
 def make_options(setup: str = "SDS", seed: int = 0, q: float = 0.5, acc: str = "f64") -> mpr_options:
-    """setup = X_S X_E X_F, e.g. 'DDD', 'SDS', 'SSS', 'HDS', 'BDS'."""
-    if len(setup) != 3 or setup[0] not in STORE or setup[1] not in PREC or setup[2] not in PREC:
+    """setup = X_S X_E X_F, e.g. 'DDD', 'SDS', 'SSS', 'HDS', 'BDS', 'HDH'."""
+    if len(setup) != 3 or setup[0] not in STORE or setup[1] not in PREC or setup[2] not in FUNC:
         raise ValueError(f"bad precision setup {setup!r}")
-    return mpr_options(seed, q, STORE[setup[0]], PREC[setup[1]], PREC[setup[2]], ACC[acc])
+    return mpr_options(seed, q, STORE[setup[0]], PREC[setup[1]], FUNC[setup[2]], ACC[acc])
 
 
 def mpr_set_options(h, setup: str = "SDS", seed: int = 0, q: float = 0.5, acc: str = "f64"):

@@ -283,7 +283,9 @@ mpr_status validate_options(const mpr_options* o)
     if (!o) return fail(MPR_ERR_INVALID_ARG, "options pointer is NULL");
     if (o->store < 0 || o->store > 3) return fail(MPR_ERR_INVALID_ARG, "store %d out of range", o->store);
     if (o->energy < 0 || o->energy > 1) return fail(MPR_ERR_INVALID_ARG, "energy %d out of range", o->energy);
-    if (o->func < 0 || o->func > 1) return fail(MPR_ERR_INVALID_ARG, "func %d out of range", o->func);
+    if (o->func < 0 || o->func > 2) return fail(MPR_ERR_INVALID_ARG, "func %d out of range", o->func);
+    if (o->func == MPR_PREC_H && o->store != MPR_STORE_F16)
+        return fail(MPR_ERR_INVALID_ARG, "FP16 functions (func = H) need FP16 spin storage");
     if (o->acc < 0 || o->acc > 1) return fail(MPR_ERR_INVALID_ARG, "acc %d out of range", o->acc);
     if (!(o->q >= 0.0 && o->q <= 1.0)) return fail(MPR_ERR_INVALID_ARG, "q = %g outside (0, 1]", o->q);
     return MPR_OK;
@@ -301,7 +303,7 @@ mpr_status init_state(mpr_ctx* h)
         if (p.acc == 0) {
             CHECK(dalloc(h, &h->acc[c], accd_bytes(h)));
             CU(cudaMemsetAsync(h->acc[c], 0, accd_bytes(h), h->stream));
-            if (p.store == kF16 && p.func == 1) {   // exact fixed-point partials (tile kernel)
+            if (p.store == kF16 && p.func >= 1) {   // exact fixed-point partials (tile kernel)
                 CHECK(dalloc(h, &h->part32[c], accf_bytes(h)));
                 CU(cudaMemsetAsync(h->part32[c], 0, accf_bytes(h), h->stream));
             }
@@ -486,7 +488,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     const bool adapt = h->prop_on && h->prop_target > 0.0 && !(flags & kSample);
     a.width = h->prop_on ? h->scal + 14 : nullptr;
     a.accepted = adapt ? prop_count(h) : nullptr;
-    const bool f32 = h->prec.func == 1;
+    const bool f32 = h->prec.func != 0;   // FP32 (or FP16) functions: the tile kernels
     const int nblk = f32 ? sweep_f32_blocks(h->L) : sweep_blocks(h->L, h->prec);
     const bool timed = h->prof && flags == 0;
     if (timed) {
@@ -625,6 +627,8 @@ mpr_status mpr_set_options(mpr_handle h, const mpr_options* opt)
 {
     if (!h) return fail(MPR_ERR_INVALID_ARG, "handle is NULL");
     CHECK(validate_options(opt));
+    if (opt->func == MPR_PREC_H && h->prop_on)
+        return fail(MPR_ERR_INVALID_ARG, "FP16 functions run uniform proposals only");
     free_state(h);   // sizes depend on the old precision
     h->opt = *opt;
     if (h->opt.q == 0.0) h->opt.q = 0.5;
@@ -981,6 +985,8 @@ mpr_status mpr_set_proposal(mpr_handle h, double width, double target)
         return fail(MPR_ERR_INVALID_ARG, "proposal half-width %g outside [0, 2 pi]", width);
     if (!(target >= 0.0) || target >= 1.0)
         return fail(MPR_ERR_INVALID_ARG, "target acceptance %g outside [0, 1)", target);
+    if (width > 0.0 && h->prec.func == MPR_PREC_H)
+        return fail(MPR_ERR_INVALID_ARG, "FP16 functions run uniform proposals only");
     CHECK(sync(h));
     h->prop_on = width > 0.0;
     h->prop_target = h->prop_on ? target : 0.0;

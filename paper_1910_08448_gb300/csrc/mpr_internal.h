@@ -36,7 +36,7 @@ enum Store : int { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 struct Precision {
     int store;      // Store
     int energy;     // 0 = FP64, 1 = FP32
-    int func;       // 0 = FP64, 1 = FP32 intrinsics
+    int func;       // 0 = FP64, 1 = FP32 intrinsics, 2 = FP16 arithmetic where safe (FP16 spins)
     int acc;        // 0 = FP64, 1 = Kahan FP32
 };
 
@@ -90,6 +90,8 @@ cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st
 int sweep_f32_blocks(const Layout& L);
 cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_sweep_f32_prop(const Precision& p, const SweepArgs& a, cudaStream_t st);
+// FP16-function setting (func 2, FP16 spins, uniform proposals only).
+cudaError_t launch_sweep_f32_half(const Precision& p, const SweepArgs& a, cudaStream_t st);
 // TMA kernel: maps for the layout and storage (false when the lattice is too small for its boxes,
 // or the driver has no tensor maps; the one-tile-per-block kernel then runs); the launch of a
 // plain pass (no kMeasure, no kSample) on nsm SMs.

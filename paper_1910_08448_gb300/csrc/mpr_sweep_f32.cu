@@ -13,6 +13,7 @@ int sweep_f32_blocks(const Layout& L)
 
 cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st)
 {
+    if (p.func == 2) return launch_sweep_f32_half(p, a, st);
     if (a.width) return launch_sweep_f32_prop(p, a, st);
     return sweep_f32_detail::launch_store<false>(p, a, st);
 }

@@ -27,23 +27,23 @@ constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 // tile of the same height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the
 // batched kernels do: the energy partials, and so the energies, stay bit-identical between the
 // two paths.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, int QM>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, int QM, bool HM>
 __device__ __forceinline__ void block_tile(const SweepArgs& a, int b, TileSmem<R>& sm, void* eslot)
 {
     const int ntx = (a.Lxh + kTJ - 1) / kTJ;
     const int tx = b % ntx, ty = b / ntx;
     const int rem = a.Lxh - tx * kTJ;
     if (tx == ntx - 1 && rem <= 32)
-        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32, QM>(
+        sweep_tile<S, R / 4, MEASURE, SAMPLE, true, true, PROP, 32, QM, HM>(
             a, 4 * tx, ty, *reinterpret_cast<TileSmem<R / 4, 32>*>(&sm), eslot);
     else if (tx == ntx - 1 && rem <= 64)
-        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64, QM>(
+        sweep_tile<S, R / 2, MEASURE, SAMPLE, true, true, PROP, 64, QM, HM>(
             a, 2 * tx, ty, *reinterpret_cast<TileSmem<R / 2, 64>*>(&sm), eslot);
     else
-        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, QM>(a, tx, ty, sm, eslot);
+        sweep_tile<S, R, MEASURE, SAMPLE, true, true, PROP, kTJ, QM, HM>(a, tx, ty, sm, eslot);
 }
 
-template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, bool HM = false>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
                                        : ((PROP && (MEASURE || SAMPLE || sizeof(S) == 4)) ? 3 : 4))
     sweep_f32_kernel(const SweepArgs a)
@@ -60,16 +60,16 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2
     // FP32 spins the second copy would spill registers)
     if constexpr (!MEASURE && SAMPLE == 0 && sizeof(S) == 2) {
         if (a.qf == 0.5f) {
-            block_tile<S, R, MEASURE, SAMPLE, PROP, 2>(a, b, sm, eslot);
+            block_tile<S, R, MEASURE, SAMPLE, PROP, 2, HM>(a, b, sm, eslot);
             return;
         }
     }
-    block_tile<S, R, MEASURE, SAMPLE, PROP, 0>(a, b, sm, eslot);
+    block_tile<S, R, MEASURE, SAMPLE, PROP, 0, HM>(a, b, sm, eslot);
 }
 
 // Launched as a programmatic dependent launch: while the previous pass's last blocks finish, this
 // pass's blocks are scheduled and load their own rows (see sweep_tile).
-template <typename S, bool MEASURE, int SAMPLE, bool PROP>
+template <typename S, bool MEASURE, int SAMPLE, bool PROP, bool HM = false>
 cudaError_t go(const SweepArgs& a, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg{};
@@ -82,31 +82,33 @@ cudaError_t go(const SweepArgs& a, cudaStream_t st)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_f32_kernel<S, kRows, MEASURE, SAMPLE, PROP>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_f32_kernel<S, kRows, MEASURE, SAMPLE, PROP, HM>, a);
 }
 
-template <typename S, bool PROP>
+template <typename S, bool PROP, bool HM = false>
 cudaError_t dispatch_mode(const Precision& p, const SweepArgs& a, cudaStream_t st)
 {
     const bool measure = (a.flags & kMeasure) && a.colour == 1;
     const int sample = (a.flags & kSample) ? (p.acc == 0 ? (a.part32 ? 3 : 1) : 2) : 0;
     if constexpr (sizeof(S) == 2) {   // fixed-point partial sums: FP16 spins only
-        if (sample == 3) return measure ? go<S, true, 3, PROP>(a, st) : go<S, false, 3, PROP>(a, st);
+        if (sample == 3)
+            return measure ? go<S, true, 3, PROP, HM>(a, st) : go<S, false, 3, PROP, HM>(a, st);
     }
     if (sample == 3) return cudaErrorInvalidValue;
     if (measure) {
-        if (sample == 0) return go<S, true, 0, PROP>(a, st);
-        if (sample == 1) return go<S, true, 1, PROP>(a, st);
-        return go<S, true, 2, PROP>(a, st);
+        if (sample == 0) return go<S, true, 0, PROP, HM>(a, st);
+        if (sample == 1) return go<S, true, 1, PROP, HM>(a, st);
+        return go<S, true, 2, PROP, HM>(a, st);
     }
-    if (sample == 0) return go<S, false, 0, PROP>(a, st);
-    if (sample == 1) return go<S, false, 1, PROP>(a, st);
-    return go<S, false, 2, PROP>(a, st);
+    if (sample == 0) return go<S, false, 0, PROP, HM>(a, st);
+    if (sample == 1) return go<S, false, 1, PROP, HM>(a, st);
+    return go<S, false, 2, PROP, HM>(a, st);
 }
 
 template <bool PROP>
 cudaError_t launch_store(const Precision& p, const SweepArgs& a, cudaStream_t st)
 {
+    if (p.func == 2) return cudaErrorInvalidValue;   // FP16 functions: launch_sweep_f32_half
     switch (p.store) {
     case kF64: return dispatch_mode<double, PROP>(p, a, st);
     case kF32: return dispatch_mode<float, PROP>(p, a, st);

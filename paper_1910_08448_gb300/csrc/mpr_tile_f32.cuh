@@ -126,6 +126,33 @@ __device__ __forceinline__ float2 atan2_doubled2(float2 y, float2 x)
     return make_float2(copysignf(r0, xy.x), copysignf(r1, xy.y));
 }
 
+// atan2_doubled2 in the FP16-function setting (X_F = H: FP16 arithmetic where it is safe, the
+// paper's future work of Sec. 3): the field is rounded to FP16, and the ratio of its smaller to
+// its larger component and the polynomial run in half2 arithmetic, both sites per instruction.
+// The polynomial has 3 coefficients (a*P(a^2) ~ 2 atan(a) on [0, 1], fitted for this library by
+// Lawson's iteratively reweighted least squares, rounded to FP16): 1.2e-3 rad minimax, 2.4e-3 rad
+// evaluated in FP16, near the FP16 spacing of the result (9.8e-4 on [1, 2)). PTX has no FP16
+// reciprocal, so the larger component's reciprocal is the FP32 one. The fold pi - 2t and the
+// sign stay in FP32: pi (and 2 pi in the later wraps) rounded to FP16 would shift every
+// reflection that uses it by about 1e-3 rad in the same direction.
+__device__ __forceinline__ float2 atan2_doubled_h2(float2 y, float2 x)
+{
+    const __half2 xh = __float22half2_rn(x), yh = __float22half2_rn(y);
+    const __half2 axh = __habs2(xh), ayh = __habs2(yh);
+    const __half2 mx = __hmax2(axh, ayh), mn = __hmin2(axh, ayh);
+    const float2 mxf = __half22float2(mx);
+    const __half2 a = __hmul2(mn, __floats2half2_rn(rcp_approx(mxf.x), rcp_approx(mxf.y)));
+    const __half2 s = __hmul2(a, a);
+    __half2 p = __hfma2(__float2half2_rn(0.15869140625f), s, __float2half2_rn(-0.5771484375f));
+    p = __hfma2(p, s, __float2half2_rn(1.990234375f));
+    const float2 t2 = __half22float2(__hmul2(a, p));
+    const float2 u = sub2(splat(3.14159265358979324f), t2);
+    const float2 ax = __half22float2(axh), ay = __half22float2(ayh);
+    const float r0 = ay.x > ax.x ? u.x : t2.x, r1 = ay.y > ax.y ? u.y : t2.y;
+    const float2 xy = mul2(x, y);
+    return make_float2(copysignf(r0, xy.x), copysignf(r1, xy.y));
+}
+
 template <typename S> struct Raw4;
 template <> struct Raw4<__half> { using T = uint2; };
 template <> struct Raw4<__nv_bfloat16> { using T = uint2; };
@@ -347,7 +374,7 @@ __device__ __forceinline__ void carry_call1(GroupCarry& gc, const uint4& w)
 // 2 q = 1/2 (the paper's value) at compile time: q*phi of the accepted angle is the proposal's
 // or the old angle's product (both computed for the energy), and r/q is r + r (exact).
 template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, int OPAR, bool PROP, int QM,
-          int TJ, int ROW>
+          int TJ, int ROW, bool HM>
 __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, int jb, int lj,
                                            Pack4<S>& pk, uint32_t bits, const TileSmem<R, TJ>& sm,
                                            double& e_d, float& e_f, float pw, int& n_acc,
@@ -496,9 +523,10 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
         float2 r;   // in [-pi - 2 pi q, pi]
         if constexpr (QH) {
             const float2 qf1 = make_float2(acc0 ? qp.x : qf.x, acc1 ? qp.y : qf.y);   // q * f1, exact
-            r = sub2(atan2_doubled2<sizeof(S) == 2>(hy, hx), qf1);
+            r = sub2(HM ? atan2_doubled_h2(hy, hx) : atan2_doubled2<sizeof(S) == 2>(hy, hx), qf1);
         } else {
-            r = fma2(splat(-q), f1, atan2_doubled2<sizeof(S) == 2>(hy, hx));
+            r = fma2(splat(-q), f1,
+                     HM ? atan2_doubled_h2(hy, hx) : atan2_doubled2<sizeof(S) == 2>(hy, hx));
         }
         // r < 0 ? r + 2 pi : r, twice: the saturated product is 1 for every negative normal r
         // and 0 for r >= 0 and NaN; the FMA then adds 2 pi or 0 with the rounding of a plain
@@ -618,7 +646,8 @@ template <int R> __device__ __forceinline__ int row_of(int i, int c) { return (R
 // branch on i & 1 disappears when the caller's loop over i is unrolled).
 // With even R, i even is the first row of its Philox group (see GroupCarry) and i odd the second;
 // with odd R each row computes its group's three calls itself.
-template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, int QM, int TJ>
+template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PROP, int QM, int TJ,
+          bool HM = false>
 __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, int ly, int jb,
                                              int lj, Pack4<S>& pk, uint32_t bits,
                                              const TileSmem<R, TJ>& sm, double& e_d, float& e_f,
@@ -626,13 +655,13 @@ __device__ __forceinline__ void update_row_i(int i, const SweepArgs& a, int y, i
 {
     if constexpr (R % 2 == 0) {
         if (i & 1)
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP, QM, TJ, 1>(a, y, ly, jb, lj, pk, bits,
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 1, PROP, QM, TJ, 1, HM>(a, y, ly, jb, lj, pk, bits,
                                                                        sm, e_d, e_f, pw, n_acc, gc);
         else
-            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP, QM, TJ, 0>(a, y, ly, jb, lj, pk, bits,
+            update_row<S, R, MEASURE, SAMPLE, SCHED, 0, PROP, QM, TJ, 0, HM>(a, y, ly, jb, lj, pk, bits,
                                                                        sm, e_d, e_f, pw, n_acc, gc);
     } else {
-        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP, QM, TJ, 2>(a, y, ly, jb, lj, pk, bits, sm,
+        update_row<S, R, MEASURE, SAMPLE, SCHED, -1, PROP, QM, TJ, 2, HM>(a, y, ly, jb, lj, pk, bits, sm,
                                                                     e_d, e_f, pw, n_acc, gc);
     }
 }
@@ -676,8 +705,9 @@ __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* co
 // touched only after the wait.
 // PROP: bounded proposals of half-width *a.width; accepted ones counted into *a.accepted.
 // QM: 1 the caller has checked q <= 1/2 (one 2 pi wrap of the reflected angle suffices); 2 q = 1/2.
+// HM: FP16-function setting (the field's doubled angle in half2 arithmetic, atan2_doubled_h2).
 template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false,
-          bool PROP = false, int TJ = kTJ, int QM = 0>
+          bool PROP = false, int TJ = kTJ, int QM = 0, bool HM = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
@@ -731,7 +761,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + row0 + row_of<R>(i - 1, c) >= a.Ly)
             group_carry_only<SCHED>(a, y, jb, gc);
         if (y < a.Ly)
-            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM>(i, a, y, ly, jb, lj, mine[i], bits[i],
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM, TJ, HM>(i, a, y, ly, jb, lj, mine[i], bits[i],
                                                              sm, e_d, e_f, pw, n_acc, gc);
     }
     if (PROP && a.accepted) count_accepted(n_acc, a.accepted);

@@ -20,7 +20,7 @@ import mpr_inputs
 pytestmark = pytest.mark.gpu
 
 TWO_PI = 2.0 * math.pi
-SETUPS_ALL = ["DDD", "SDS", "SSS", "SDD", "DDS", "HDS", "BDS", "HSS"]
+SETUPS_ALL = ["DDD", "SDS", "SSS", "SDD", "DDS", "HDS", "BDS", "HSS", "HDH"]
 
 
 @pytest.fixture(scope="module")
@@ -245,6 +245,66 @@ def test_single_sweep_16bit_storage(mpr, orc, excusal_log, Lx, Ly, p, setup):
     excusal_log(setup + " black", excused[col == 1].sum(), (col == 1).sum(),
                 black_b * (col == 1).sum())
     assert excused[col == 1].mean() < black_b
+
+
+# FP16 functions (HDH): as HDS, except that the doubled field angle of the over-relaxation is
+# FP16 arithmetic. Its error is at most 3.4e-3 rad (2.4e-3 from the FP16 polynomial and result,
+# 1e-3 from the FP16 rounding of the FP32 field components, which turns the field by at most
+# 2^-11 rad whatever |h|), so an over-relaxed angle phi' = 2 r moves by up to 6.8e-3 rad; with
+# both sides rounded to FP16 the results agree within 2^-8 + 6.8e-3. Sites whose over-relaxation
+# decision lies within 4e-3 of the domain boundary (or whose Metropolis decision lies within 1e-4)
+# are excused; the black pass starts from the GPU's red result on both sides.
+HDH_TOL = 2.0**-8 + 6.8e-3
+HDH_OR_MARGIN = 4e-3
+
+
+@pytest.mark.parametrize("Lx,Ly,p", [(64, 64, 0.33), (131, 37, 0.9), (300, 45, 0.66),
+                                     (2100, 1300, 0.9)])
+def test_single_sweep_fp16_functions(mpr, orc, excusal_log, Lx, Ly, p):
+    T = 0.5
+    pr = mpr_inputs.make_problem(Lx, Ly, p, field_seed=19, mask_seed=20)
+    o, state = _start_state(orc, pr, "HDH", 8)
+    got, _, info, _, _ = _gpu_sweeps(mpr, pr, "HDH", 8, state, 40, T, 1)
+    assert info["sweep_kernel"] == 0
+    red, mm_r, om_r = o.half_sweep(state, pr.mask, T, 40, 0)
+    red_r = _round_store(red, "HDH")
+    col = _colour(Lx, Ly)
+    bad_r = (mm_r < 1e-4) | (om_r < HDH_OR_MARGIN)
+    sel = (col == 0) & ~bad_r
+    d = np.abs(got - red_r)
+    assert np.all(d[sel] <= HDH_TOL), d[sel].max()
+    # black pass: the oracle's black update from the GPU's own red result (red values that differ
+    # within the tolerance would otherwise move the black fields)
+    start_b = np.where(col == 0, got, state)
+    blk, mm_b, om_b = o.half_sweep(start_b, pr.mask, T, 40, 1)
+    bad_b = (col == 1) & ((mm_b < 1e-4) | (om_b < HDH_OR_MARGIN))
+    sel = (col == 1) & ~bad_b
+    d = np.abs(got - _round_store(blk, "HDH"))
+    assert np.all(d[sel] <= HDH_TOL), d[sel].max()
+    bad_r = (col == 0) & bad_r
+    excusal_log("HDH red", bad_r.sum(), (col == 0).sum(), 0.05 * (col == 0).sum())
+    excusal_log("HDH black", bad_b.sum(), (col == 1).sum(), 0.05 * (col == 1).sum())
+    assert bad_r.sum() <= 0.05 * (col == 0).sum() and bad_b.sum() <= 0.05 * (col == 1).sum()
+    m = pr.mask == 1
+    assert np.array_equal(got[m], state[m])
+
+
+def test_fp16_functions_option_errors(mpr):
+    pr = mpr_inputs.make_problem(64, 48, 0.5, field_seed=1, mask_seed=2)
+    h = mpr.mpr_create(pr.z, pr.mask)
+    try:
+        for bad in ("SDH", "BDH", "DDH"):   # FP16 functions need FP16 spins
+            with pytest.raises(mpr.MPRError) as e:
+                mpr.mpr_set_options(h, bad)
+            assert e.value.status == mpr.MPR_ERR_INVALID_ARG
+        mpr.mpr_set_options(h, "HDH")
+        with pytest.raises(mpr.MPRError) as e:   # uniform proposals only
+            mpr.mpr_set_proposal(h, 0.5, 0.4)
+        assert e.value.status == mpr.MPR_ERR_INVALID_ARG
+        with pytest.raises(mpr.MPRError):        # no TMA kernel for FP16 functions
+            mpr.mpr_set_sweep_kernel(h, 1)
+    finally:
+        mpr.mpr_destroy(h)
 
 
 # --- energies, trajectories, predictions ---------------------------------------------------

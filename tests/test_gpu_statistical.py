@@ -69,7 +69,7 @@ def oracle_config1(orc):
 
 @pytest.mark.parametrize("setup,acc", [("DDD", "f64"), ("SDS", "f64"), ("SSS", "f64"),
                                        ("HDS", "f64"), ("BDS", "f64"), ("SDS", "kahan"),
-                                       ("HSS", "kahan")])
+                                       ("HSS", "kahan"), ("HDH", "f64")])
 def test_config1_within_one_percent_of_oracle(mpr, orc, oracle_config1, gap_log, setup, acc):
     g_mae, g_rmse, g_e, o_mae, o_rmse, o_e = [], [], [], [], [], []
     for s, (pr, mae, rmse, e, T) in zip(SEEDS, oracle_config1):
@@ -128,7 +128,8 @@ def config3_fp64(mpr):
     return out
 
 
-@pytest.mark.parametrize("setup,acc", [("HDS", "f64"), ("BDS", "f64"), ("HDS", "kahan")])
+@pytest.mark.parametrize("setup,acc", [("HDS", "f64"), ("BDS", "f64"), ("HDS", "kahan"),
+                                       ("HDH", "f64")])
 def test_config3_16bit_storage_vs_fp64_gpu_ten_seeds(mpr, config3_fp64, gap_log, setup, acc):
     rows = []
     for s, (pr, md, rd, ed) in zip(SEEDS, config3_fp64):
