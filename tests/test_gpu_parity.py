@@ -630,6 +630,18 @@ def test_tma_kernel_equals_tile_kernel(mpr, orc, Lx, Ly, p, setup):
     assert i0["e_bond_mean"] == i1["e_bond_mean"]
 
 
+@pytest.mark.parametrize("Lx,Ly,setup", [(4096, 2048, "HDS"), (2100, 1301, "SDS"), (4096, 4096, "HDS")])
+def test_tma_kernel_equals_tile_kernel_over_many_sweeps(mpr, orc, Lx, Ly, setup):
+    # The two FP32 sweep kernels over 200 sweeps with several waves of tiles (and an odd Ly, whose
+    # last Philox group of rows has one row): identical chains, bit for bit.
+    pr = mpr_inputs.make_problem(Lx, Ly, 0.9, field_seed=43, mask_seed=44)
+    _, state = _start_state(orc, pr, setup, 33)
+    g0, s0, i0, _ = _kernel_run(mpr, pr, setup, state, 0, 200, 0, T=0.07)
+    g1, s1, i1, _ = _kernel_run(mpr, pr, setup, state, 1, 200, 0, T=0.07)
+    assert i0["sweep_kernel"] == 0 and i1["sweep_kernel"] == 1 and s0 == s1 == 205
+    assert np.array_equal(g0, g1)
+
+
 def test_sweep_kernel_choice(mpr, orc):
     pr = mpr_inputs.make_problem(700, 300, 0.9, field_seed=43, mask_seed=44)
     _, state = _start_state(orc, pr, "HDS", 31)
