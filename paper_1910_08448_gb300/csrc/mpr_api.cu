@@ -130,6 +130,7 @@ struct mpr_ctx {
     int sweep_force = -1;                // mpr_set_sweep_kernel: -1 automatic, 0, 1
     long long stall_ns = 0;              // mpr_inject_tma_stall: wait limit of the next TMA pass
     int sweep_kind = -1;                 // automatic choice (-1 until made)
+    int nsplit = 0;                      // plain passes of the tile kernel: last tiles split in two
     // bounded Metropolis proposals (mpr_set_proposal): the half-width lives on the device in
     // scal[14], the acceptance counter of the adaptation in scal[13]
     bool prop_on = false;
@@ -314,6 +315,18 @@ mpr_status init_state(mpr_ctx* h)
             CU(cudaMemsetAsync(h->acc_lo[c], 0, accf_bytes(h), h->stream));
         }
     }
+    // Last wave of the tile kernel's plain passes: with T tiles and S resident blocks on the
+    // device, the last T mod S tiles would run as a partial wave; when twice that many blocks
+    // still fit one wave (and no tile column is narrow), they run as half-height tiles. Only for
+    // lattices of fewer than four waves, where the partial one is a large share of the pass
+    // (4096^2: 2048 tiles on 608 blocks, 2 % faster; at 8192^2 it measured 1 % slower).
+    h->nsplit = 0;
+    if (p.func != 0 && h->L.Lxh % 128 == 0) {
+        const int slots = sweep_f32_plain_occupancy(p) * h->nsm;
+        const int nt = sweep_f32_blocks(h->L);
+        const int rem = slots > 0 ? nt % slots : 0;
+        if (rem > 0 && 2 * rem <= slots && nt < 4 * slots) h->nsplit = rem;
+    }
     // TMA maps for the FP32-function kernel (false: the lattice is too narrow for its boxes)
     h->tma = TmaMaps{};
     if (p.func == 1) make_sweep_maps(h->L, p.store, h->ang, h->mb, &h->tma);
@@ -484,6 +497,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.err = dev_err(h);
     a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds
     a.stall_test = 0;
+    a.nsplit = (flags == 0) ? h->nsplit : 0;   // plain passes of the tile kernel only
     // bounded proposals; the width adapts after every sweep that does not sample
     const bool adapt = h->prop_on && h->prop_target > 0.0 && !(flags & kSample);
     a.width = h->prop_on ? h->scal + 14 : nullptr;

@@ -72,6 +72,8 @@ struct SweepArgs {
                                // (NULL: uniform proposals)
     unsigned long long* accepted;  // bounded proposals: accepted proposals of the pass's
                                    // prediction sites are added here (NULL: not counted)
+    int nsplit;                // one-tile-per-block FP32 kernel, plain passes: the last nsplit
+                               // tiles run as two half-height tiles each (0: none)
 };
 
 // TMA descriptors of one problem's half-lattices for the TMA-fed FP32 sweep kernel: per colour c
@@ -88,6 +90,8 @@ struct TmaMaps {
 int sweep_blocks(const Layout& L, const Precision& p);
 cudaError_t launch_sweep(const Precision& p, const SweepArgs& a, cudaStream_t st);
 int sweep_f32_blocks(const Layout& L);
+// Resident blocks per SM of the plain pass of the one-tile-per-block FP32 kernel.
+int sweep_f32_plain_occupancy(const Precision& p);
 cudaError_t launch_sweep_f32(const Precision& p, const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_sweep_f32_prop(const Precision& p, const SweepArgs& a, cudaStream_t st);
 // FP16-function setting (func 2, FP16 spins, uniform proposals only).

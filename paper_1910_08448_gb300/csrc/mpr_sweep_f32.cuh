@@ -27,10 +27,28 @@ constexpr int kRows = 4;      // rows per thread of the tiles (128 x 32)
 // tile of the same height (tile column 4 tx in 32-column units, 2 tx in 64-column units), as the
 // batched kernels do: the energy partials, and so the energies, stay bit-identical between the
 // two paths.
+//
+// Last wave (plain passes, a.nsplit > 0): the grid has nsplit blocks more than tiles; the last
+// nsplit tiles run as two half-height tiles each (16 rows, blocks taken in pairs), so the final
+// partial wave of blocks has twice as many, half as long: less of the machine idles while it
+// drains. The host splits only when the half-lattice has no narrow last tile column and twice the
+// remainder still fits one wave.
 template <typename S, int R, bool MEASURE, int SAMPLE, bool PROP, int QM, bool HM>
 __device__ __forceinline__ void block_tile(const SweepArgs& a, int b, TileSmem<R>& sm, void* eslot)
 {
     const int ntx = (a.Lxh + kTJ - 1) / kTJ;
+    if constexpr (!MEASURE && SAMPLE == 0) {
+        if (a.nsplit > 0) {
+            const int nfull = (int)gridDim.x - 2 * a.nsplit;   // tiles that run whole
+            if (b >= nfull) {
+                const int k = b - nfull, t = nfull + (k >> 1);
+                sweep_tile<S, R / 2, false, 0, true, true, PROP, kTJ, QM, HM>(
+                    a, t % ntx, 2 * (t / ntx) + (k & 1), *reinterpret_cast<TileSmem<R / 2>*>(&sm),
+                    eslot);
+                return;
+            }
+        }
+    }
     const int tx = b % ntx, ty = b / ntx;
     const int rem = a.Lxh - tx * kTJ;
     if (tx == ntx - 1 && rem <= 32)
@@ -73,7 +91,8 @@ template <typename S, bool MEASURE, int SAMPLE, bool PROP, bool HM = false>
 cudaError_t go(const SweepArgs& a, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>()));
+    cfg.gridDim = dim3(((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + tile_rows<kRows>() - 1) / tile_rows<kRows>())
+                       + ((!MEASURE && SAMPLE == 0) ? a.nsplit : 0));
     cfg.blockDim = dim3(32, kWarps);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;

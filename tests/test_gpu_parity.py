@@ -630,10 +630,13 @@ def test_tma_kernel_equals_tile_kernel(mpr, orc, Lx, Ly, p, setup):
     assert i0["e_bond_mean"] == i1["e_bond_mean"]
 
 
-@pytest.mark.parametrize("Lx,Ly,setup", [(4096, 2048, "HDS"), (2100, 1301, "SDS"), (4096, 4096, "HDS")])
+@pytest.mark.parametrize("Lx,Ly,setup", [(4096, 2048, "HDS"), (2100, 1301, "SDS"), (4096, 4096, "HDS"),
+                                          (2048, 1024, "SDS")])
 def test_tma_kernel_equals_tile_kernel_over_many_sweeps(mpr, orc, Lx, Ly, setup):
     # The two FP32 sweep kernels over 200 sweeps with several waves of tiles (and an odd Ly, whose
-    # last Philox group of rows has one row): identical chains, bit for bit.
+    # last Philox group of rows has one row): identical chains, bit for bit. At 4096^2 the tile
+    # kernel's plain passes run their last 224 tiles as half-height tiles, at 2048 x 1024 all of
+    # them (one partial wave); the TMA kernel never splits.
     pr = mpr_inputs.make_problem(Lx, Ly, 0.9, field_seed=43, mask_seed=44)
     _, state = _start_state(orc, pr, setup, 33)
     g0, s0, i0, _ = _kernel_run(mpr, pr, setup, state, 0, 200, 0, T=0.07)
