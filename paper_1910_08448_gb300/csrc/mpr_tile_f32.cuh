@@ -426,6 +426,7 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
                       make_float2(ds.z, ds.w));
     }
     float ev[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // MEASURE: u_b . h_b of the row's sites
+    float fsamp[4];                            // SAMPLE: the row's sampled angles (0: frozen)
     // Random numbers (see GroupCarry), whether or not the sites update: no branch per site.
     // ROW 0: first row of the group; 1: second row (gc from the first); 2: the thread's only row
     // of the group (odd rows per thread: the group's other row belongs to another thread), whose
@@ -560,31 +561,10 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             if (upd[k1]) pk.s[k1] = store_from<S>(fn.y);
             fn = make_float2(load_as<float>(pk.s[k0]), load_as<float>(pk.s[k1]));
         }
-        // the site's angle after the move, as stored (SAMPLE and MEASURE use it)
-        const float fs[2] = {fn.x, fn.y};
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            const int k = k0 + l;
-            if (SAMPLE == 1) {
-                if (upd[k]) a.acc[idx + k] += (double)fs[l];
-            } else if (SAMPLE == 2) {
-                if (upd[k]) {
-                    // Kahan: hi carries the sum, lo the (negated) lost low-order part
-                    const float hi = a.acc_hi[idx + k], lo = a.acc_lo[idx + k];
-                    const float yv = fs[l] - lo;
-                    const float tt = hi + yv;
-                    a.acc_lo[idx + k] = (tt - hi) - yv;
-                    a.acc_hi[idx + k] = tt;
-                }
-            } else if (SAMPLE == 3) {
-                // FP16 spins, FP64 sums: f is an FP16 value, an integer multiple of 2^-24 below
-                // 2^3, so f * 2^24 converts to an int exactly and 16 of them fit an int32; the
-                // handle folds the partial into the FP64 sum, where every add is exact (the sum
-                // stays a multiple of 2^-24 below 2^29): the same bits as adding f itself, with a
-                // 4-byte read and write per sample instead of 8-byte ones
-                if (upd[k]) a.part32[idx + k] += __float2int_rn(fs[l] * 16777216.0f);
-            }
-        }
+        // the site's angle after the move, as stored (SAMPLE and MEASURE use it); a frozen site
+        // (or padding) contributes 0 to the sums below, which leaves them unchanged
+        fsamp[k0] = upd[k0] ? fn.x : 0.0f;
+        fsamp[k1] = upd[k1] ? fn.y : 0.0f;
         if (MEASURE) {
             // every bond joins a red and a black site: sum over black sites of u_b . h_b
             const float2 qn = mul2(splat(q), fn);
@@ -595,6 +575,47 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
             ev[k0] = ex[k0] ? e2.x : 0.0f;
             ev[k1] = ex[k1] ? e2.y : 0.0f;
         }
+    }
+    // Sampling: the row's four sums updated by one vector read and write (the thread's columns
+    // are 4-aligned, rows 128-aligned); frozen sites add 0.
+    if constexpr (SAMPLE == 1) {
+        double2* p = reinterpret_cast<double2*>(a.acc + idx);
+        double2 s0 = p[0], s1 = p[1];
+        s0.x += (double)fsamp[0];
+        s0.y += (double)fsamp[1];
+        s1.x += (double)fsamp[2];
+        s1.y += (double)fsamp[3];
+        p[0] = s0;
+        p[1] = s1;
+    } else if constexpr (SAMPLE == 2) {
+        // Kahan: hi carries the sum, lo the (negated) lost low-order part
+        float4* ph = reinterpret_cast<float4*>(a.acc_hi + idx);
+        float4* pl = reinterpret_cast<float4*>(a.acc_lo + idx);
+        const float4 h4 = *ph, l4 = *pl;
+        const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+        float nh[4], nl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float yv = fsamp[k] - lv[k];
+            const float tt = hv[k] + yv;
+            nl[k] = (tt - hv[k]) - yv;
+            nh[k] = tt;
+        }
+        *ph = make_float4(nh[0], nh[1], nh[2], nh[3]);
+        *pl = make_float4(nl[0], nl[1], nl[2], nl[3]);
+    } else if constexpr (SAMPLE == 3) {
+        // FP16 spins, FP64 sums: f is an FP16 value, an integer multiple of 2^-24 below 2^3, so
+        // f * 2^24 converts to an int exactly and 16 of them fit an int32; the handle folds the
+        // partial into the FP64 sum, where every add is exact (the sum stays a multiple of 2^-24
+        // below 2^29): the same bits as adding f itself, with a 4-byte read and write per sample
+        // instead of 8-byte ones
+        int4* p = reinterpret_cast<int4*>(a.part32 + idx);
+        int4 v = *p;
+        v.x += __float2int_rn(fsamp[0] * 16777216.0f);
+        v.y += __float2int_rn(fsamp[1] * 16777216.0f);
+        v.z += __float2int_rn(fsamp[2] * 16777216.0f);
+        v.w += __float2int_rn(fsamp[3] * 16777216.0f);
+        *p = v;
     }
     if (MEASURE) {
         // the row's four FP32 terms pairwise in FP32 (two roundings of the size of the terms'
