@@ -1,12 +1,13 @@
 // mpr_sweep_tma.cu -- single-problem colour half-sweep for the FP32 function setting, sweep kernel
-// kind 1, plain passes: persistent blocks (3 per SM) walk 128 x 32 tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; while a block updates tile t, the TMA unit copies the next tile's
-// three boxes (other colour with halo, own values, own frozen bits) into shared memory, completing
-// on one mbarrier, so the staging step is pure sin/cos work. Blocks that walk equal tiles stay in
-// step with each other (all convert, then all update), and the static tile split leaves part of
-// the last round idle; the handle keeps this kernel only where its own timing finds it faster
-// than kind 0 (mpr_sweep_f32.cu). Also the tensor maps (cuTensorMapEncodeTiled through the
-// runtime's driver entry point).
+// kind 1, plain passes: persistent blocks (as many per SM as the shared memory allows: 4 with
+// 16-bit spins) walk 128 x 32 tiles u = blockIdx.x, blockIdx.x + gridDim.x, ...; while a block
+// updates tile u, the TMA unit copies the next tile's three boxes (other colour with halo, own
+// values, own frozen bits) into shared memory, completing on one mbarrier, so the staging step is
+// pure sin/cos work. When the tiles left after the whole rounds of the grid fit one round as
+// halves, they run as half-height units, so the last round takes half as long. Blocks that walk
+// equal tiles stay in step with each other (all convert, then all update); the handle keeps this
+// kernel only where its own timing finds it faster than kind 0 (mpr_sweep_f32.cu). Also the
+// tensor maps (cuTensorMapEncodeTiled through the runtime's driver entry point).
 #include "mpr.h"
 #include "mpr_tile_f32.cuh"
 #include "mpr_tma.cuh"
@@ -38,30 +39,98 @@ template <typename S, int R> struct TmaSmem {
     int ok;
 };
 
-// Unit vectors of the other colour from the TMA box (see stage() for the global-memory form).
-template <typename S, int R, bool CHECK>
+// Unit vectors of the other colour from the TMA box (see stage() for the global-memory form), for
+// a tile of RT rows per thread (RT = R, or R / 2 for a half-height tile, which uses the box's
+// first TY / 2 + 2 rows).
+template <typename S, int R, int RT, bool CHECK>
 __device__ __forceinline__ void convert(const SweepArgs& a, const TmaSmem<S, R>& sm, int y0,
-                                        int j0, int jb, int lj, int cb, float q, TileSmem<R>& t)
+                                        int j0, int jb, int lj, int cb, float q, TileSmem<RT>& t)
 {
     using Sm = TmaSmem<S, R>;
-    constexpr int NR = (Sm::TY + 2 + kWarps - 1) / kWarps;
+    constexpr int TYT = kWarps * RT;
+    constexpr int NR = (TYT + 2 + kWarps - 1) / kWarps;
     const int lane = threadIdx.x, warp = threadIdx.y;
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int r = warp + i * kWarps;
-        if (r >= Sm::TY + 2) break;
+        if (r >= TYT + 2) break;
         const int y = y0 - 1 + r;
         Pack4<S> st;
         load4(&sm.other[r][Sm::HL + lj], st);
         const S halo = sm.other[r][lane == 0 ? Sm::HL - 1 : Sm::HL + kTJ];
-        unit_row<S, R, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st, halo, t);
+        unit_row<S, RT, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st, halo, t);
+    }
+}
+
+// Origin of work unit u of a pass: units below nfull are whole tiles in row-major order; unit
+// nfull + k is half k & 1 (the upper or lower TY / 2 rows) of tile nfull + (k >> 1).
+struct Unit {
+    int j0, y0;
+    bool half;
+};
+__device__ __forceinline__ Unit unit_of(int u, int nfull, int ntx, int TY)
+{
+    if (u < nfull) return {(u % ntx) * kTJ, (u / ntx) * TY, false};
+    const int k = u - nfull, t = nfull + (k >> 1);
+    return {(t % ntx) * kTJ, (t / ntx) * TY + (k & 1) * (TY / 2), true};
+}
+
+// One work unit of RT rows per thread whose boxes have landed: own values and bits to registers,
+// unit vectors of the other colour, a block barrier, the next unit's copies (leader, next >= 0),
+// then the update of the unit's rows.
+template <typename S, int R, int RT, int QM, typename Issue>
+__device__ __forceinline__ void tma_unit(const SweepArgs& a, TmaSmem<S, R>& sm, int j0, int y0,
+                                         int next, bool leader, Issue&& issue)
+{
+    constexpr int TYT = kWarps * RT;
+    TileSmem<RT>& t = *reinterpret_cast<TileSmem<RT>*>(&sm.t);
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int lj = 4 * lane, jb = j0 + lj;
+    const int cb = a.colour ^ 1;
+    Pack4<S> mine[RT];
+    uint32_t bits[RT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {   // rows in the order row_of()
+        const int ly = warp * RT + row_of<RT>(i, a.colour);
+        load4(&sm.own[ly][lj], mine[i]);
+        bits[i] = (sm.mbits[ly][lane >> 3] >> (lj & 31)) & 0xFu;
+    }
+    const bool interior = y0 >= 1 && y0 + TYT < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
+    const float qs = QM == 2 ? 0.5f : a.qf;
+    if (interior) convert<S, R, RT, false>(a, sm, y0, j0, jb, lj, cb, qs, t);
+    else convert<S, R, RT, true>(a, sm, y0, j0, jb, lj, cb, qs, t);
+    __syncthreads();   // unit vectors complete; the boxes are free for the next unit
+    if (leader && next >= 0) {
+        tma::fence_proxy_async();
+        issue(next);
+    }
+
+    double e_d = 0.0;   // unused: no energy in plain passes
+    float e_f = 0.0f;
+    int n_acc = 0;      // unused: uniform proposals only
+    GroupCarry gc{0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+        const int ly = warp * RT + row_of<RT>(i, a.colour);
+        const int y = y0 + ly;
+        if (RT % 2 == 0 && (i & 1) && y < a.Ly && y0 + warp * RT + row_of<RT>(i - 1, a.colour) >= a.Ly)
+            group_carry_only<true>(a, y, jb, gc);
+        if (y < a.Ly)
+            update_row_i<S, RT, false, 0, true, false, QM>(i, a, y, ly, jb, lj, mine[i], bits[i], t,
+                                                          e_d, e_f, 0.0f, n_acc, gc);
     }
 }
 
 // Plain passes only (no fused energy, no sampling): the handle runs those passes with
-// sweep_f32_kernel, whose per-tile energy partials it reduces.
-template <typename S, int R>
-__global__ void __launch_bounds__(256, 3)
+// sweep_f32_kernel, whose per-tile energy partials it reduces. QM as in sweep_tile (2: q = 1/2 at
+// compile time, the 16-bit storages only). Blocks per SM as the shared memory allows: 4 with
+// 16-bit spins (64 registers), 3 with FP32 and 2 with FP64 spins.
+// Launched as a programmatic dependent launch: the leader issues the first tile's own-colour and
+// mask copies (the own colour was last written two passes back, which has completed), every
+// thread waits for the previous pass, the next pass is released, and only then is the other
+// colour copied; results are written after the block barrier that follows.
+template <typename S, int R, int QM>
+__global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : (sizeof(S) == 4 ? 3 : 2))
     sweep_f32_tma_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap m_other,
                          const __grid_constant__ CUtensorMap m_own,
                          const __grid_constant__ CUtensorMap m_mask)
@@ -70,22 +139,22 @@ __global__ void __launch_bounds__(256, 3)
     constexpr int TY = Sm::TY;
     extern __shared__ __align__(128) unsigned char dsm[];
     Sm& sm = *reinterpret_cast<Sm*>(dsm);
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    const bool leader = lane == 0 && warp == 0;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     const int ntx = (a.Lxh + kTJ - 1) / kTJ;
     const int ntiles = ntx * ((a.Ly + TY - 1) / TY);
-    const int cb = a.colour ^ 1;
-    const int lj = 4 * lane;
+    const int nfull = ntiles - a.nsplit;          // the last nsplit tiles run as two halves each
+    const int nunits = nfull + 2 * a.nsplit;
 
-    // one thread issues the three copies of tile t; x offsets are multiples of 16 bytes
-    auto issue = [&](int t) {
-        const int j0 = (t % ntx) * kTJ, y0 = (t / ntx) * TY;
+    // one thread issues the three copies of unit u (full-height boxes also for a half tile);
+    // x offsets are multiples of 16 bytes
+    auto issue = [&](int u) {
+        const Unit w = unit_of(u, nfull, ntx, TY);
         tma::arrive_expect_tx(&sm.bar, Sm::kBytes);
-        tma::load_2d(&sm.other[0][0], &m_other, &sm.bar, j0 - Sm::HL, y0 - 1);
-        tma::load_2d(&sm.own[0][0], &m_own, &sm.bar, j0, y0);
-        tma::load_2d(&sm.mbits[0][0], &m_mask, &sm.bar, j0 / 32, y0);
+        tma::load_2d(&sm.other[0][0], &m_other, &sm.bar, w.j0 - Sm::HL, w.y0 - 1);
+        tma::load_2d(&sm.own[0][0], &m_own, &sm.bar, w.j0, w.y0);
+        tma::load_2d(&sm.mbits[0][0], &m_mask, &sm.bar, w.j0 / 32, w.y0);
     };
-    // the leader waits for tile `it`'s copies; a wait that runs out records the error, waits once
+    // the leader waits for unit `it`'s copies; a wait that runs out records the error, waits once
     // more for the copy in flight, and stops the block at the next barrier
     auto await = [&](uint32_t it) {
         if (!tma::wait(&sm.bar, it & 1u, a.wait_ns)) {
@@ -95,65 +164,46 @@ __global__ void __launch_bounds__(256, 3)
         }
     };
 
-    int t = blockIdx.x;
+    int u = blockIdx.x;
+    const bool first = leader && u < nunits && !(a.stall_test && blockIdx.x == 0);
     if (leader) {
         sm.ok = 1;
         tma::mbar_init(&sm.bar, 1);
-        if (t < ntiles) {
-            if (!(a.stall_test && blockIdx.x == 0)) issue(t);
-            await(0);
+    }
+    if (first) {
+        const Unit w = unit_of(u, nfull, ntx, TY);
+        tma::arrive_expect_tx(&sm.bar, Sm::kBytes);
+        tma::load_2d(&sm.own[0][0], &m_own, &sm.bar, w.j0, w.y0);
+        tma::load_2d(&sm.mbits[0][0], &m_mask, &sm.bar, w.j0 / 32, w.y0);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous pass is complete
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (leader && u < nunits) {
+        if (first) {
+            const Unit w = unit_of(u, nfull, ntx, TY);
+            tma::load_2d(&sm.other[0][0], &m_other, &sm.bar, w.j0 - Sm::HL, w.y0 - 1);
         }
+        await(0);
     }
     __syncthreads();
-    for (uint32_t it = 0; t < ntiles; ++it) {
+    for (uint32_t it = 0; u < nunits; ++it) {
         if (!sm.ok) return;   // uniform: read after a block barrier
-        const int j0 = (t % ntx) * kTJ, y0 = (t / ntx) * TY;
-        const int jb = j0 + lj;
-        Pack4<S> mine[R];
-        uint32_t bits[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {   // rows in the order row_of()
-            const int ly = warp * R + row_of<R>(i, a.colour);
-            load4(&sm.own[ly][lj], mine[i]);
-            bits[i] = (sm.mbits[ly][lane >> 3] >> (lj & 31)) & 0xFu;
-        }
-        const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + kTJ) + 1 < a.Lx;
-        if (interior) convert<S, R, false>(a, sm, y0, j0, jb, lj, cb, a.qf, sm.t);
-        else convert<S, R, true>(a, sm, y0, j0, jb, lj, cb, a.qf, sm.t);
-        __syncthreads();   // unit vectors complete; the boxes are free for the next tile
-        const int tn = t + (int)gridDim.x;
-        if (leader && tn < ntiles) {
-            tma::fence_proxy_async();
-            issue(tn);
-        }
-
-        double e_d = 0.0;   // unused: no energy in plain passes
-        float e_f = 0.0f;
-        int n_acc = 0;      // unused: uniform proposals only
-        GroupCarry gc{0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int ly = warp * R + row_of<R>(i, a.colour);
-            const int y = y0 + ly;
-            if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + warp * R + row_of<R>(i - 1, a.colour) >= a.Ly)
-                group_carry_only<true>(a, y, jb, gc);
-            if (y < a.Ly)
-                update_row_i<S, R, false, 0, true, false, false>(i, a, y, ly, jb, lj, mine[i],
-                                                                 bits[i], sm.t, e_d, e_f, 0.0f,
-                                                                 n_acc, gc);
-        }
-        if (leader && tn < ntiles) await(it + 1);
+        const Unit w = unit_of(u, nfull, ntx, TY);
+        const int un = u + (int)gridDim.x;
+        const int next = un < nunits ? un : -1;
+        if (R % 2 == 0 && w.half) tma_unit<S, R, R / 2, QM>(a, sm, w.j0, w.y0, next, leader, issue);
+        else tma_unit<S, R, R, QM>(a, sm, w.j0, w.y0, next, leader, issue);
+        if (leader && next >= 0) await(it + 1);
         __syncthreads();   // the unit vectors' readers are done; sm.ok is current
-        t = tn;
+        u = un;
     }
 }
 
-template <typename S>
-cudaError_t go_tma(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t st)
+template <typename S, int QM>
+cudaError_t go_tma_q(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t st)
 {
-    if (a.flags & (kMeasure | kSample)) return cudaErrorInvalidValue;   // plain passes only
     using Sm = TmaSmem<S, kTmaRows>;
-    auto kern = sweep_f32_tma_kernel<S, kTmaRows>;
+    auto kern = sweep_f32_tma_kernel<S, kTmaRows, QM>;
     // per instantiation, once: shared-memory opt-in and the resident blocks per SM
     static const int bps = [&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Sm));
@@ -164,10 +214,36 @@ cudaError_t go_tma(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t s
         return n < 1 ? 1 : n;
     }();
     const int ntiles = ((a.Lxh + kTJ - 1) / kTJ) * ((a.Ly + Sm::TY - 1) / Sm::TY);
-    const int grid = ntiles < nsm * bps ? ntiles : nsm * bps;
+    const int slots = nsm * bps;
+    // last round: when the tiles left over after whole rounds of the grid, split into halves,
+    // still fit one round, they run as half-height units (that round takes half as long)
+    SweepArgs b = a;
+    const int rem = ntiles % slots;
+    b.nsplit = (ntiles > slots && rem > 0 && 2 * rem <= slots) ? rem : 0;
+    const int nunits = ntiles + b.nsplit;
+    const int grid = nunits < slots ? nunits : slots;
     const int c = a.colour;
-    kern<<<grid, dim3(32, kWarps), sizeof(Sm), st>>>(a, m.other[c ^ 1], m.own[c], m.mask[c]);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32, kWarps);
+    cfg.dynamicSmemBytes = sizeof(Sm);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, b, m.other[c ^ 1], m.own[c], m.mask[c]);
+}
+
+template <typename S>
+cudaError_t go_tma(const SweepArgs& a, const TmaMaps& m, int nsm, cudaStream_t st)
+{
+    if (a.flags & (kMeasure | kSample)) return cudaErrorInvalidValue;   // plain passes only
+    if constexpr (sizeof(S) == 2) {
+        if (a.qf == 0.5f) return go_tma_q<S, 2>(a, m, nsm, st);
+    }
+    return go_tma_q<S, 0>(a, m, nsm, st);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()

@@ -631,12 +631,16 @@ def test_tma_kernel_equals_tile_kernel(mpr, orc, Lx, Ly, p, setup):
 
 
 @pytest.mark.parametrize("Lx,Ly,setup", [(4096, 2048, "HDS"), (2100, 1301, "SDS"), (4096, 4096, "HDS"),
-                                          (2048, 1024, "SDS")])
+                                          (2048, 1024, "SDS"), (2100, 2200, "HDS"),
+                                          (4096, 1200, "SDS")])
 def test_tma_kernel_equals_tile_kernel_over_many_sweeps(mpr, orc, Lx, Ly, setup):
     # The two FP32 sweep kernels over 200 sweeps with several waves of tiles (and an odd Ly, whose
-    # last Philox group of rows has one row): identical chains, bit for bit. At 4096^2 the tile
-    # kernel's plain passes run their last 224 tiles as half-height tiles, at 2048 x 1024 all of
-    # them (one partial wave); the TMA kernel never splits.
+    # last Philox group of rows has one row): identical chains, bit for bit. On a 152-SM GPU, at
+    # 4096^2 both kernels run the last 224 tiles of a plain pass as half-height tiles, the tile
+    # kernel at 2048 x 1024 all of them (one partial wave). The persistent TMA kernel (4 blocks per
+    # SM with 16-bit spins, 3 with FP32) also splits at 2100 x 2200 (621 tiles, the last 13 split,
+    # ragged last tile column and row) and at 4096 x 1200 (608 tiles on 456 blocks: the last 152
+    # split, the lower halves of the last tile row lie wholly below the lattice).
     pr = mpr_inputs.make_problem(Lx, Ly, 0.9, field_seed=43, mask_seed=44)
     _, state = _start_state(orc, pr, setup, 33)
     g0, s0, i0, _ = _kernel_run(mpr, pr, setup, state, 0, 200, 0, T=0.07)
