@@ -12,6 +12,8 @@ __global__ void __launch_bounds__(256) finish_kernel(const Args* __restrict__ A,
     __shared__ int s_scan[256];
     Ctl* ctl = A->ctl;
     const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
+    // the black pass (a programmatic edge) has completed: its bookkeeping is visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (__ldcg(&ctl->changed)) {   // a problem finished in this sweep: shrink the tile list
         const int sel = __ldcg(&ctl->list_sel);
         compact_list(A, A->lists + (size_t)sel * A->ntiles, __ldcg(&ctl->n_list),
@@ -35,13 +37,13 @@ namespace {
 
 batch::Kernels kernels_for(int store, int shape)
 {
-    if (shape < 0 || shape >= batch::kShapes) return batch::Kernels{nullptr, nullptr, 0};
+    if (shape < 0 || shape >= batch::kShapes) return batch::Kernels{nullptr, nullptr, 0, nullptr};
     switch (store) {
     case kF64: return batch::kernels_f64(shape);
     case kF32: return batch::kernels_f32(shape);
     case kF16: return batch::kernels_f16(shape);
     case kBF16: return batch::kernels_bf16(shape);
-    default: return batch::Kernels{nullptr, nullptr, 0};
+    default: return batch::Kernels{nullptr, nullptr, 0, nullptr};
     }
 }
 
@@ -87,12 +89,31 @@ cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args
     return e;
 }
 
-cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::Args* args_dev,
-                              const PhiloxSched& keys, cudaGraphExec_t* out)
+namespace {
+
+// A kernel node of `body` after `dep` (none if null); programmatic: the node may launch once
+// every block of `dep` has released it (griddepcontrol.launch_dependents) or exited.
+cudaError_t add_kernel(cudaGraphNode_t* node, cudaGraph_t body, const cudaGraphNode_t* dep,
+                       bool programmatic, const void* func, int grid, size_t smem, void** params)
 {
-    const batch::Kernels kk = kernels_for(store, shape);
-    const void* pass = kk.pass;
-    if (!pass || max_tiles < 1) return cudaErrorInvalidValue;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeKernel;
+    np.kernel.func = const_cast<void*>(func);
+    np.kernel.gridDim = dim3(grid);
+    np.kernel.blockDim = dim3(32, f32::kWarps);
+    np.kernel.sharedMemBytes = (unsigned)smem;
+    np.kernel.kernelParams = params;
+    cudaGraphEdgeData ed{};
+    if (programmatic) {
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+    }
+    return cudaGraphAddNode(node, body, dep, dep ? &ed : nullptr, dep ? 1 : 0, &np);
+}
+
+cudaError_t graph_build(const void* pass, size_t smem, int max_tiles, bool programmatic,
+                        const batch::Args* args_dev, const PhiloxSched& keys, cudaGraphExec_t* out)
+{
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
@@ -110,37 +131,36 @@ cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
     const int red = 0, black = 1;
+    void* params_r[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&red),
+                        const_cast<PhiloxSched*>(&keys)};
+    void* params_b[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&black),
+                        const_cast<PhiloxSched*>(&keys)};
+    void* params_f[] = {const_cast<batch::Args**>(&args_dev), &loop};
     cudaGraphNode_t n_red, n_black, n_fin;
-    if (e == cudaSuccess) {
-        void* params[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&red),
-                          const_cast<PhiloxSched*>(&keys)};
-        cudaKernelNodeParams kp{};
-        kp.func = const_cast<void*>(pass);
-        kp.gridDim = dim3(max_tiles);
-        kp.blockDim = dim3(32, f32::kWarps);
-        kp.sharedMemBytes = (unsigned)kk.smem;
-        kp.kernelParams = params;
-        e = cudaGraphAddKernelNode(&n_red, body, nullptr, 0, &kp);
-        if (e == cudaSuccess) {
-            void* params_b[] = {const_cast<batch::Args**>(&args_dev), const_cast<int*>(&black),
-                                const_cast<PhiloxSched*>(&keys)};
-            kp.kernelParams = params_b;
-            e = cudaGraphAddKernelNode(&n_black, body, &n_red, 1, &kp);
-        }
-    }
-    if (e == cudaSuccess) {
-        void* params[] = {const_cast<batch::Args**>(&args_dev), &loop};
-        cudaKernelNodeParams kp{};
-        kp.func = reinterpret_cast<void*>(&batch::finish_kernel);
-        kp.gridDim = dim3(1);
-        kp.blockDim = dim3(32, f32::kWarps);
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = params;
-        e = cudaGraphAddKernelNode(&n_fin, body, &n_black, 1, &kp);
-    }
+    if (e == cudaSuccess) e = add_kernel(&n_red, body, nullptr, false, pass, max_tiles, smem, params_r);
+    if (e == cudaSuccess)
+        e = add_kernel(&n_black, body, &n_red, programmatic, pass, max_tiles, smem, params_b);
+    if (e == cudaSuccess)
+        e = add_kernel(&n_fin, body, &n_black, programmatic,
+                       reinterpret_cast<const void*>(&batch::finish_kernel), 1, 0, params_f);
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     return e;
+}
+
+}  // namespace
+
+cudaError_t batch_graph_build(int store, int shape, int max_tiles, bool qhalf,
+                              const batch::Args* args_dev, const PhiloxSched& keys,
+                              cudaGraphExec_t* out)
+{
+    const batch::Kernels kk = kernels_for(store, shape);
+    const void* pass = (qhalf && kk.pass_qhalf) ? kk.pass_qhalf : kk.pass;
+    if (!pass || max_tiles < 1) return cudaErrorInvalidValue;
+    if (graph_build(pass, kk.smem, max_tiles, true, args_dev, keys, out) == cudaSuccess)
+        return cudaSuccess;
+    cudaGetLastError();   // the runtime refused the programmatic edges: plain ones
+    return graph_build(pass, kk.smem, max_tiles, false, args_dev, keys, out);
 }
 
 }  // namespace mpr

@@ -94,11 +94,13 @@ constexpr int shape_rows(int s) { return 8 * (128 / kShape[s].cols) * kShape[s].
 constexpr int shape_cols(int s) { return kShape[s].cols; }
 
 // The kernels of one storage type and tile shape: graph-mode pass kernel, persistent kernel, and
-// their dynamic shared memory. One function per storage type (mpr_batch_<type>.cu).
+// their dynamic shared memory; pass_qhalf is the pass kernel compiled for q = 1/2 (16-bit
+// storages only, else null). One function per storage type (mpr_batch_<type>.cu).
 struct Kernels {
     const void* pass;
     const void* persistent;
     size_t smem;
+    const void* pass_qhalf;
 };
 Kernels kernels_f16(int shape);
 Kernels kernels_bf16(int shape);
@@ -114,7 +116,12 @@ cudaError_t batch_launch(int store, int shape, int grid, const batch::Args* args
                          const PhiloxSched& keys, cudaStream_t st, bool use_graph);
 // Graph mode: an executable graph whose device-side while loop runs red pass, black pass and the
 // finish kernel until no problem is active (or max_iters). max_tiles = blocks of a pass kernel.
-cudaError_t batch_graph_build(int store, int shape, int max_tiles, const batch::Args* args_dev,
-                              const PhiloxSched& keys, cudaGraphExec_t* out);
+// qhalf: the batch's q is 1/2 (the pass kernels compiled for it, where the storage has them).
+// The black pass and the finish kernel hang on programmatic edges (each may start while its
+// predecessor's last blocks run, and waits for it before reading its results); where the
+// runtime refuses such edges, plain ones.
+cudaError_t batch_graph_build(int store, int shape, int max_tiles, bool qhalf,
+                              const batch::Args* args_dev, const PhiloxSched& keys,
+                              cudaGraphExec_t* out);
 
 }  // namespace mpr

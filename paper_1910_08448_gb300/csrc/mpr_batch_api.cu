@@ -71,6 +71,7 @@ struct mpr_batch_ctx {
                                              // device-side while loop
     cudaGraphExec_t gexec[batch::kShapes] = {};   // graph-mode executables per tile shape
     int gexec_tiles[batch::kShapes] = {};
+    bool gexec_qhalf[batch::kShapes] = {};
     int tiled_shape = -1;                    // tile shape of the current tile list
     int bar_extra = 0;
     double timeout_s = 2.0;
@@ -282,13 +283,15 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
         BCU(cudaMemcpyAsync(b->dArgs, &A, sizeof A, cudaMemcpyHostToDevice, b->stream));
         if (b->use_graph == 2) {
             cudaGraphExec_t& ge = b->gexec[b->shape];
-            if (ge && b->gexec_tiles[b->shape] != b->ntiles) {
+            const bool qhalf = A.qf == 0.5f;
+            if (ge && (b->gexec_tiles[b->shape] != b->ntiles || b->gexec_qhalf[b->shape] != qhalf)) {
                 cudaGraphExecDestroy(ge);
                 ge = nullptr;
             }
             if (!ge) {
-                BCU(batch_graph_build(b->prec.store, b->shape, b->ntiles, b->dArgs, keys, &ge));
+                BCU(batch_graph_build(b->prec.store, b->shape, b->ntiles, qhalf, b->dArgs, keys, &ge));
                 b->gexec_tiles[b->shape] = b->ntiles;
+                b->gexec_qhalf[b->shape] = qhalf;
             }
             BCU(cudaGraphLaunch(ge, b->stream));
         } else {

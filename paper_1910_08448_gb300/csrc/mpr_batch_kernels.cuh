@@ -225,7 +225,7 @@ __device__ void bookkeeping(Prob& P, const Args& A, double raw)
 // arguments are a pointer and scalars, so nothing passes through local memory. ks (SCHED): the
 // kernel parameter holding the batch's Philox round keys (one seed for every problem), so they
 // enter the rounds as constant operands; the counter-dependent half of round 1 is formed per tile.
-template <typename S, int R, int TJ, bool MEASURE, int SAMPLE, bool SCHED>
+template <typename S, int R, int TJ, bool MEASURE, int SAMPLE, bool SCHED, int QM = 0>
 __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int p, int colour,
                                           int tx, int ty, const PhiloxSched* ks)
 {
@@ -265,8 +265,10 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
         a.ph.c = (((uint32_t)p << 8) | (kTagMetropolis << 1) | (uint32_t)colour) ^ a.seed_hi;
     }
     void* eslot = MEASURE ? static_cast<char*>(A->epart) + (size_t)t * (A->energy_f32 ? 4 : 8) : nullptr;
-    sweep_tile<S, R, MEASURE, SAMPLE, SCHED>(a, tx, ty,
-                                             *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
+    // PDL: own values first, then the wait for the previous kernel (a no-op unless it hangs on a
+    // programmatic edge, and in the persistent kernel), then the release of the next one
+    sweep_tile<S, R, MEASURE, SAMPLE, SCHED, true, false, TJ, QM>(
+        a, tx, ty, *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
 }
 
 template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
@@ -276,14 +278,15 @@ __device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, i
     tile_body<S, R, TJ, MEASURE, SAMPLE, false>(A, t, p, colour, tx, ty, nullptr);
 }
 
-// The variant of a tile of shape (R, TJ) for this pass: plain inlined, the others as calls.
-template <typename S, int R, int TJ>
+// The variant of a tile of shape (R, TJ) for this pass: plain inlined (QM as in sweep_tile), the
+// others as calls.
+template <typename S, int R, int TJ, int QM>
 __device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, int p, int colour,
                                              int tx, int ty, bool measure, bool sample,
                                              const PhiloxSched& ks)
 {
     if (!measure && !sample) {
-        tile_body<S, R, TJ, false, 0, true>(A, t, p, colour, tx, ty, &ks);
+        tile_body<S, R, TJ, false, 0, true, QM>(A, t, p, colour, tx, ty, &ks);
     } else if (measure && !sample) {
         tile_fn<S, R, TJ, true, 0>(A, t, p, colour, tx, ty);
     } else if (!measure) {
@@ -297,7 +300,7 @@ __device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, 
 
 // Tile t of problem p. The plain pass (no energy, no sampling: most passes) is inlined; the rarer
 // variants are calls.
-template <typename S, int R, int TJ>
+template <typename S, int R, int TJ, int QM = 0>
 __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p, int colour,
                                         TileSmem<R, TJ>& sm, const PhiloxSched& ks)
 {
@@ -317,19 +320,19 @@ __device__ __forceinline__ void do_tile(const Args* __restrict__ A, int t, int p
     const bool last = tx == P.ntx - 1;
     if constexpr (kTail32) {
         if (last && P.tail == 32) {
-            tile_variant<S, R / 4, 32>(A, t, p, colour, 4 * tx, ty, measure, sample, ks);
+            tile_variant<S, R / 4, 32, QM>(A, t, p, colour, 4 * tx, ty, measure, sample, ks);
         } else if (last && P.tail == 64) {
-            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
+            tile_variant<S, R / 2, 64, QM>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
         } else {
-            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
+            tile_variant<S, R, TJ, QM>(A, t, p, colour, tx, ty, measure, sample, ks);
         }
     } else if constexpr (kTail) {
         if (last && P.tail == 64)
-            tile_variant<S, R / 2, 64>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
+            tile_variant<S, R / 2, 64, QM>(A, t, p, colour, 2 * tx, ty, measure, sample, ks);
         else
-            tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
+            tile_variant<S, R, TJ, QM>(A, t, p, colour, tx, ty, measure, sample, ks);
     } else {
-        tile_variant<S, R, TJ>(A, t, p, colour, tx, ty, measure, sample, ks);
+        tile_variant<S, R, TJ, QM>(A, t, p, colour, tx, ty, measure, sample, ks);
     }
     if (colour == 1) {
         __shared__ int s_last;
@@ -463,7 +466,12 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Args* __restrict__ 
 
 // Compiled for 4 resident blocks per SM: the inlined plain tile (most passes) fits 64 registers;
 // the rarer energy and sampling variants are calls that may spill.
-template <typename S, int R, int TJ>
+// QM: 2 for the batch's q = 1/2 (16-bit storages), else 0 (see sweep_tile).
+// The tile list, its length and the problems' phases were last written by the finish kernel and
+// the black pass of the previous sweep, which have completed before a red pass starts (the red
+// pass is the first node of the loop body) and before a black pass starts (it hangs on the red
+// pass, which released it only after its own wait): a block reads them before its wait.
+template <typename S, int R, int TJ, int QM>
 __global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A, int colour,
                                                        const PhiloxSched ks)
 {
@@ -472,7 +480,7 @@ __global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A
     const int k = blockIdx.x;
     if (k >= __ldcg(&ctl->n_list)) return;
     const int2 e = __ldcg(A->lists + (size_t)__ldcg(&ctl->list_sel) * A->ntiles + k);
-    do_tile<S, R, TJ>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R, TJ>*>(dsm), ks);
+    do_tile<S, R, TJ, QM>(A, e.x, e.y, colour, *reinterpret_cast<TileSmem<R, TJ>*>(dsm), ks);
 }
 
 
@@ -480,8 +488,11 @@ __global__ void __launch_bounds__(256, 4) pass_kernel(const Args* __restrict__ A
 template <typename S, int R, int TJ>
 Kernels entry()
 {
-    return Kernels{reinterpret_cast<const void*>(&pass_kernel<S, R, TJ>),
-                   reinterpret_cast<const void*>(&batch_kernel<S, R, TJ>), sizeof(TileSmem<R, TJ>)};
+    const void* qh = nullptr;
+    if constexpr (sizeof(S) == 2) qh = reinterpret_cast<const void*>(&pass_kernel<S, R, TJ, 2>);
+    return Kernels{reinterpret_cast<const void*>(&pass_kernel<S, R, TJ, 0>),
+                   reinterpret_cast<const void*>(&batch_kernel<S, R, TJ>), sizeof(TileSmem<R, TJ>),
+                   qh};
 }
 
 template <typename S>
@@ -493,7 +504,7 @@ Kernels table(int s)
     case 2: return entry<S, 4, 128>();
     case 3: return entry<S, 1, 64>();
     case 4: return entry<S, 2, 64>();
-    default: return Kernels{nullptr, nullptr, 0};
+    default: return Kernels{nullptr, nullptr, 0, nullptr};
     }
 }
 
