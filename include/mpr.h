@@ -286,6 +286,8 @@ mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, 
                           int* status_out);
 mpr_status mpr_batch_predict(mpr_batch b, int i, double* out);          /* host, Lx*Ly doubles */
 mpr_status mpr_batch_get_state(mpr_batch b, int i, double* angles, uint32_t* sweep);
+/* Problem i's info as mpr_get_info gives a handle's; e_bond_mean is the mean over the sampling
+ * sweeps of the latest fill that sampled, n_samples counts the sampling sweeps of every fill. */
 mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info);
 /* The last fill's launch: iterations (sweeps of the longest-running problem), device time in ms
  * (CUDA events on the batch's stream), and the launch shape and mode it used. Any pointer may be

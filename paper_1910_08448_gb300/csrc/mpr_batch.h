@@ -16,13 +16,16 @@ struct Dyn {
     int np;                     // probes finished
     int kind;                   // probe kind: 0 = T_lo, 1 = T_hi, 2 = bisection midpoint
     int status;                 // MPR_OK or MPR_ERR_TUNE_NO_CONVERGE
-    int nsamples;               // sampling sweeps accumulated
+    int nsamples;               // sampling sweeps accumulated (every fill)
+    int nfill;                  // sampling sweeps of the latest fill that sampled
     unsigned sweep;             // Philox sweep index of the next sweep
     float invTf;                // 1/T in FP32 for the tile kernel
     double T;                   // temperature of the current probe / of the run
     double lo, hi, mid;         // bisection bracket in log T, current midpoint
     double esum;                // sum of e_b over the measured sweeps of the current probe
-    double esamp;               // sum of e_b over the sampling sweeps
+    double esamp;               // sum of e_b over the sampling sweeps of the latest fill that
+                                // sampled (its mean is the problem's e_bond_mean, as a single
+                                // handle reports the mean over its latest run with samples)
     unsigned long long site_updates;
 };
 
@@ -70,6 +73,9 @@ struct Args {
     double* acc;                // FP64 accumulator pool (acc_kind 0)
     float* acc_hi;              // Kahan pools (acc_kind 1)
     float* acc_lo;
+    int* part32;                // 16-bit storage with acc_kind 0: exact int32 partials of the
+                                // sampled angles (units of 2^-24), folded into acc every 16
+                                // samples and after the last; null otherwise
     void* epart;                // one energy partial per tile
     Ctl* ctl;
     int n_eq, n_meas, max_probes;

@@ -100,6 +100,7 @@ struct mpr_batch_ctx {
     double* acc = nullptr;
     float* acc_hi = nullptr;
     float* acc_lo = nullptr;
+    int* part32 = nullptr;                   // int32 sample partials (16-bit storage, FP64 sums)
     void* epart = nullptr;
     double* zpool = nullptr;
     unsigned char* mpool = nullptr;
@@ -134,7 +135,7 @@ void bfree_all(mpr_batch_ctx* b)
 {
     for (auto& g : b->gexec)
         if (g) cudaGraphExecDestroy(g);
-    void* ptrs[] = {b->d_lists, b->dArgs, b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo,
+    void* ptrs[] = {b->d_lists, b->dArgs, b->dP, b->ctl, b->d_tile_prob, b->ang, b->mb, b->acc, b->acc_hi, b->acc_lo, b->part32,
                     b->epart, b->zpool, b->mpool, b->range, b->scal, b->part, b->tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -254,6 +255,7 @@ mpr_status launch_fill(mpr_batch_ctx* b, bool tune, int equil, int samples, floa
     A.acc = b->acc;
     A.acc_hi = b->acc_hi;
     A.acc_lo = b->acc_lo;
+    A.part32 = b->part32;
     A.epart = b->epart;
     A.ctl = b->ctl;
     A.n_eq = b->tune.n_eq;
@@ -330,7 +332,6 @@ void prepare_fill(mpr_batch_ctx* b, const double* T)
         d.invTf = (float)(1.0 / (T ? T[i] : b->tune.T_lo));
         d.status = MPR_OK;
         d.esum = 0.0;
-        d.esamp = 0.0;
         d.step = 0;
         d.lo = log(b->tune.T_lo);
         d.hi = log(b->tune.T_hi);
@@ -446,6 +447,11 @@ mpr_status mpr_batch_create(int n, const int* Lx, const int* Ly, const double* c
         if ((s = balloc(b, &b->acc, (size_t)b->acc_elems * 8)) != MPR_OK) return bail(s);
         if (cudaMemset(b->acc, 0, (size_t)b->acc_elems * 8) != cudaSuccess)
             return bail(bfail(MPR_ERR_CUDA, "memset failed"));
+        if (o.store == MPR_STORE_F16) {   // exact fixed-point sample partials (FP16 values)
+            if ((s = balloc(b, &b->part32, (size_t)b->acc_elems * 4)) != MPR_OK) return bail(s);
+            if (cudaMemset(b->part32, 0, (size_t)b->acc_elems * 4) != cudaSuccess)
+                return bail(bfail(MPR_ERR_CUDA, "memset failed"));
+        }
     } else {
         if ((s = balloc(b, &b->acc_hi, (size_t)b->acc_elems * 4)) != MPR_OK ||
             (s = balloc(b, &b->acc_lo, (size_t)b->acc_elems * 4)) != MPR_OK)
@@ -575,11 +581,14 @@ mpr_status mpr_batch_fill(mpr_batch b, const double* T, int equil, int samples, 
             if (!(T[i] > 0.0) || !isfinite(T[i]))
                 return bfail(MPR_ERR_INVALID_ARG, "problem %d: temperature %g must be > 0", i, T[i]);
     prepare_fill(b, T);
-    if (T)
-        for (int i = 0; i < b->n; ++i) {
-            batch::Dyn& d = b->P[(size_t)i].d;
-            d.phase = equil > 0 ? batch::kRunEquil : (samples > 0 ? batch::kRunSample : batch::kDone);
+    for (int i = 0; i < b->n; ++i) {
+        batch::Dyn& d = b->P[(size_t)i].d;
+        if (T) d.phase = equil > 0 ? batch::kRunEquil : (samples > 0 ? batch::kRunSample : batch::kDone);
+        if (samples > 0) {   // this fill's samples give the mean bond energy
+            d.esamp = 0.0;
+            d.nfill = 0;
         }
+    }
     BCHECK(launch_fill(b, T == nullptr, equil, samples, nullptr));
     int worst = MPR_OK;
     for (int i = 0; i < b->n; ++i) {
@@ -732,7 +741,7 @@ mpr_status mpr_batch_get_info(mpr_batch b, int i, mpr_info* info)
     info->sweep = p.d.sweep;
     info->n_samples = p.d.nsamples;
     info->n_probes = p.d.np;
-    info->e_bond_mean = p.d.nsamples > 0 ? p.d.esamp / (double)p.d.nsamples : NAN;
+    info->e_bond_mean = p.d.nfill > 0 ? p.d.esamp / (double)p.d.nfill : NAN;
     info->site_updates = p.d.site_updates;
     info->device_bytes = b->bytes;
     info->kernel_launches = b->launches;

@@ -17,6 +17,8 @@
 // leaves, the kernel ends normally and the host reports MPR_ERR_DEVICE_TIMEOUT.
 #pragma once
 
+#include <type_traits>
+
 #include "mpr.h"
 #include "mpr_batch.h"
 #include "mpr_tile_f32.cuh"
@@ -142,6 +144,7 @@ __device__ void load_dyn(const Prob& P, Dyn& d)
     d.kind = __ldcg(&P.d.kind);
     d.status = __ldcg(&P.d.status);
     d.nsamples = __ldcg(&P.d.nsamples);
+    d.nfill = __ldcg(&P.d.nfill);
     d.sweep = __ldcg(&P.d.sweep);
     d.invTf = __ldcg(&P.d.invTf);
     d.T = __ldcg(&P.d.T);
@@ -204,6 +207,7 @@ __device__ void bookkeeping(Prob& P, const Args& A, double raw)
     case kRunSample:
         d.esamp += e;
         d.nsamples += 1;
+        d.nfill += 1;
         if (++d.step >= A.samples) {
             d.phase = kDone;
             atomicSub(&A.ctl->n_active, 1);
@@ -238,6 +242,7 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
     a.acc = A->acc ? A->acc + P.acc_off[colour] : nullptr;
     a.acc_hi = A->acc_hi ? A->acc_hi + P.acc_off[colour] : nullptr;
     a.acc_lo = A->acc_lo ? A->acc_lo + P.acc_off[colour] : nullptr;
+    a.part32 = A->part32 ? A->part32 + P.acc_off[colour] : nullptr;
     a.epart = A->epart;
     a.Lx = P.Lx;
     a.Ly = P.Ly;
@@ -271,12 +276,55 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
         a, tx, ty, *reinterpret_cast<TileSmem<R, TJ>*>(dsm), eslot);
 }
 
+// Folds the int32 sample partials of this thread's sites of tile (tx, ty) into the FP64 sums
+// (the sites whose partials the thread itself added to in sweep_tile: its R rows, its 4 columns):
+// acc += v * 2^-24 is exact, so the sums are the bits that adding every sampled angle in FP64
+// gives (the single handle folds the same way, in a separate kernel).
+template <int R, int TJ>
+__device__ __forceinline__ void fold_tile(const Args* __restrict__ A, const Prob& P, int colour,
+                                          int tx, int ty)
+{
+    constexpr int TY = tile_rows<R, TJ>();
+    const int lc = threadIdx.x % Lanes<TJ>::kPerRow, lr = threadIdx.x / Lanes<TJ>::kPerRow;
+    const int row0 = (threadIdx.y * Lanes<TJ>::kRows + lr) * R;
+    const int jb = tx * TJ + 4 * lc;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int y = ty * TY + row0 + i;
+        if (y >= P.Ly) break;
+        const long long idx = P.acc_off[colour] + (long long)y * P.pitch + jb;
+        int4* pp = reinterpret_cast<int4*>(A->part32 + idx);
+        const int4 v = *pp;
+        if ((v.x | v.y | v.z | v.w) == 0) continue;
+        double2* q = reinterpret_cast<double2*>(A->acc + idx);
+        double2 s0 = q[0], s1 = q[1];
+        s0.x += (double)v.x * 0x1.0p-24;
+        s0.y += (double)v.y * 0x1.0p-24;
+        s1.x += (double)v.z * 0x1.0p-24;
+        s1.y += (double)v.w * 0x1.0p-24;
+        q[0] = s0;
+        q[1] = s1;
+        *pp = make_int4(0, 0, 0, 0);
+    }
+}
+
 template <typename S, int R, int TJ, bool MEASURE, int SAMPLE>
 __device__ __noinline__ void tile_fn(const Args* __restrict__ A, int t, int p, int colour, int tx,
                                      int ty)
 {
     tile_body<S, R, TJ, MEASURE, SAMPLE, false>(A, t, p, colour, tx, ty, nullptr);
+    if constexpr (SAMPLE == 3) {
+        // sample `step` of this run (the bookkeeping advances it after both passes): 16 int32
+        // partials of angles below 8 stay below 2^31, so fold after every 16th and the last
+        const Prob& P = A->prob[p];
+        const int step = __ldcg(&P.d.step);
+        if ((step & 15) == 15 || step == A->samples - 1) fold_tile<R, TJ>(A, P, colour, tx, ty);
+    }
 }
+
+// FP16 storage: every stored angle is a multiple of 2^-24, so sampling adds exact int32 partials
+// (A->part32) instead of FP64 values.
+template <typename S> constexpr bool kFix = std::is_same<S, __half>::value;
 
 // The variant of a tile of shape (R, TJ) for this pass: plain inlined (QM as in sweep_tile), the
 // others as calls.
@@ -290,10 +338,12 @@ __device__ __forceinline__ void tile_variant(const Args* __restrict__ A, int t, 
     } else if (measure && !sample) {
         tile_fn<S, R, TJ, true, 0>(A, t, p, colour, tx, ty);
     } else if (!measure) {
-        if (A->acc_kind == 0) tile_fn<S, R, TJ, false, 1>(A, t, p, colour, tx, ty);
+        if (kFix<S> && A->part32) tile_fn<S, R, TJ, false, (kFix<S> ? 3 : 1)>(A, t, p, colour, tx, ty);
+        else if (A->acc_kind == 0) tile_fn<S, R, TJ, false, 1>(A, t, p, colour, tx, ty);
         else tile_fn<S, R, TJ, false, 2>(A, t, p, colour, tx, ty);
     } else {
-        if (A->acc_kind == 0) tile_fn<S, R, TJ, true, 1>(A, t, p, colour, tx, ty);
+        if (kFix<S> && A->part32) tile_fn<S, R, TJ, true, (kFix<S> ? 3 : 1)>(A, t, p, colour, tx, ty);
+        else if (A->acc_kind == 0) tile_fn<S, R, TJ, true, 1>(A, t, p, colour, tx, ty);
         else tile_fn<S, R, TJ, true, 2>(A, t, p, colour, tx, ty);
     }
 }

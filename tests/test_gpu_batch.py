@@ -240,23 +240,36 @@ def test_batch_errors_name_the_problem(mpr):
 
 
 def test_fixed_point_sample_sums_equal_fp64_sums(mpr):
-    # A single handle with FP16 spins and FP64 sums adds samples as exact int32 partials (units of
-    # 2^-24) folded into the FP64 sums every 16 samples and before a prediction; the batch adds
-    # each sample to FP64 directly. Both are exact, so predictions agree bit for bit -- across
-    # folds (40 samples), and with a prediction taken in between (after 21).
+    # With FP16 spins and FP64 sums both paths add samples as exact int32 partials (units of
+    # 2^-24): the single handle folds them into the FP64 sums every 16 samples and before a
+    # prediction (a separate kernel), the batch after every 16th sample and the last sample of a
+    # fill (each tile folds its own sites). Every add is exact, so predictions agree bit for bit
+    # with those of FP64 sums -- across folds (40 samples in one fill: folds after 16, 32, 40),
+    # with a prediction taken in between (after 21), and over two fills (21 + 19 samples).
     probs = _problems([(300, 200, 0.9), (64, 64, 0.33)], base=500)
     b = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "HDS", seed=13)
+    b2 = mpr.mpr_batch_create([p.z for p in probs], [p.mask for p in probs], "HDS", seed=13)
     h = mpr.mpr_create(probs[0].z, probs[0].mask)
     try:
         mpr.mpr_batch_fill(b, 10, 40, T=np.full(len(probs), 0.25))
+        mpr.mpr_batch_fill(b2, 10, 21, T=np.full(len(probs), 0.25))
+        mpr.mpr_batch_fill(b2, 0, 19, T=np.full(len(probs), 0.25))
         mpr.mpr_set_options(h, "HDS", seed=13)
         mpr.mpr_set_temperature(h, 0.25)
         mpr.mpr_run(h, 10, 21)
         mid = mpr.mpr_predict(h)
         mpr.mpr_run(h, 0, 19)
-        assert np.array_equal(mpr.mpr_predict(h), mpr.mpr_batch_predict(b, 0))
+        zh = mpr.mpr_predict(h)
+        assert np.array_equal(zh, mpr.mpr_batch_predict(b, 0))
+        assert np.array_equal(zh, mpr.mpr_batch_predict(b2, 0))
+        for i in range(len(probs)):
+            assert np.array_equal(mpr.mpr_batch_predict(b, i), mpr.mpr_batch_predict(b2, i))
         assert np.all(np.isfinite(mid))
         assert mpr.mpr_get_info(h)["n_samples"] == 40
+        assert mpr.mpr_batch_get_info(b2, 0)["n_samples"] == 40
+        # the mean bond energy is over the latest run (fill) that sampled, as a handle reports it
+        assert mpr.mpr_batch_get_info(b2, 0)["e_bond_mean"] == mpr.mpr_get_info(h)["e_bond_mean"]
     finally:
         mpr.mpr_batch_destroy(b)
+        mpr.mpr_batch_destroy(b2)
         mpr.mpr_destroy(h)
