@@ -257,18 +257,22 @@ __device__ __forceinline__ void unit_row(const SweepArgs& a, int r, int y, int j
 }
 
 // Stages the other colour's rows y0-1 .. y0+TY and columns j0-1 .. j0+TJ of a tile from global
-// memory as unit vectors. All loads are issued before the sin/cos work. The 2 (TY + 2) halo
-// entries (columns j0 - 1 and j0 + TJ) go to the block's first threads, one entry each, so no
-// warp runs a halo branch with two of its lanes.
+// memory as unit vectors. All loads are issued before the sin/cos work. The work is spread evenly
+// over the block: staged rows 0 .. TY-1 as 4-entry vectors (the same number per warp), the last
+// two rows (TY, TY+1) one entry per thread, and the 2 (TY + 2) halo entries (columns j0 - 1 and
+// j0 + TJ) one per thread of the block's first threads, so no warp converts a row more than the
+// others and none runs a halo branch with two of its lanes.
 template <typename S, int R, bool CHECK, int TJ>
 __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ other, int y0,
                                       int j0, int jb, int lj, int cb, float q, TileSmem<R, TJ>& sm)
 {
     constexpr int TY = tile_rows<R, TJ>();
     constexpr int HW = Lanes<TJ>::kRows;
-    constexpr int NR = (TY + 2 + kWarps * HW - 1) / (kWarps * HW);   // staged rows per thread
-    constexpr int NH = 2 * (TY + 2);                                  // halo entries
-    static_assert(NH <= 32 * kWarps, "one halo entry per thread");
+    static_assert(TY % (kWarps * HW) == 0, "vector rows split evenly over the warps");
+    constexpr int NR = TY / (kWarps * HW);   // vector rows per thread
+    constexpr int NH = 2 * (TY + 2);         // halo entries
+    constexpr int NE = 2 * TJ;               // entries of the last two rows
+    static_assert(NH <= 32 * kWarps && NE <= 32 * kWarps, "one entry per thread");
     const int warp = threadIdx.y;
     const int lr = threadIdx.x / Lanes<TJ>::kPerRow;
     const int tid = warp * 32 + threadIdx.x;
@@ -278,21 +282,30 @@ __device__ __forceinline__ void stage(const SweepArgs& a, const S* __restrict__ 
     const int hy = y0 - 1 + hr;
     const bool hok = tid < NH && (!CHECK || (hy >= 0 && hy < a.Ly && hj >= 0 &&
                                              2 * hj + ((hy + cb) & 1) < a.Lx));
-    S hv{};
+    // this thread's entry of the last two rows: row er = TY + tid / TJ, column j0 + tid % TJ
+    const int er = TY + tid / TJ, ej = j0 + tid % TJ;
+    const int ey = y0 - 1 + er;
+    const bool eok = tid < NE && (!CHECK || (ey < a.Ly && 2 * ej + ((ey + cb) & 1) < a.Lx));
+    S hv{}, evl{};
     if (hok) hv = other[(size_t)hy * a.pitch + hj];
+    if (eok) evl = other[(size_t)ey * a.pitch + ej];
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int r = (warp + i * kWarps) * HW + lr;
         const int y = y0 - 1 + r;
-        if (r < TY + 2 && (!CHECK || (y >= 0 && y < a.Ly)))
-            load4(other + (size_t)y * a.pitch + jb, st[i]);
+        if (!CHECK || (y >= 0 && y < a.Ly)) load4(other + (size_t)y * a.pitch + jb, st[i]);
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int r = (warp + i * kWarps) * HW + lr;
-        if (r >= TY + 2) break;
         const int y = y0 - 1 + r;
         unit_row<S, R, CHECK, TJ, false>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st[i], S{}, sm);
+    }
+    if (tid < NE) {
+        float ec = 0.0f, es = 0.0f;
+        if (eok) __sincosf(q * load_as<float>(evl), &es, &ec);
+        sm.cs[er][4 + tid % TJ] = ec;
+        sm.sn[er][4 + tid % TJ] = es;
     }
     if (tid < NH) {
         float hc = 0.0f, hs = 0.0f;
