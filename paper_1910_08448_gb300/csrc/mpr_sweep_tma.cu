@@ -41,24 +41,44 @@ template <typename S, int R> struct TmaSmem {
 
 // Unit vectors of the other colour from the TMA box (see stage() for the global-memory form), for
 // a tile of RT rows per thread (RT = R, or R / 2 for a half-height tile, which uses the box's
-// first TY / 2 + 2 rows).
+// first TY / 2 + 2 rows). As in stage(), the work is spread evenly: rows 0 .. TYT-1 as 4-entry
+// vectors (RT per warp, the halo entries by lanes 0 and 1), the last two rows one entry per
+// thread and their four halo entries by threads 0 .. 3.
 template <typename S, int R, int RT, bool CHECK>
 __device__ __forceinline__ void convert(const SweepArgs& a, const TmaSmem<S, R>& sm, int y0,
                                         int j0, int jb, int lj, int cb, float q, TileSmem<RT>& t)
 {
     using Sm = TmaSmem<S, R>;
     constexpr int TYT = kWarps * RT;
-    constexpr int NR = (TYT + 2 + kWarps - 1) / kWarps;
+    static_assert(2 * kTJ == 32 * kWarps, "one entry of the last two rows per thread");
     const int lane = threadIdx.x, warp = threadIdx.y;
+    const int tid = warp * 32 + lane;
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
+    for (int i = 0; i < RT; ++i) {
         const int r = warp + i * kWarps;
-        if (r >= TYT + 2) break;
         const int y = y0 - 1 + r;
         Pack4<S> st;
         load4(&sm.other[r][Sm::HL + lj], st);
         const S halo = sm.other[r][lane == 0 ? Sm::HL - 1 : Sm::HL + kTJ];
         unit_row<S, RT, CHECK>(a, r, y, j0, jb, lj, (y + cb) & 1, q, st, halo, t);
+    }
+    {
+        const int er = TYT + tid / kTJ, ec = tid % kTJ;
+        const int ey = y0 - 1 + er;
+        float vc = 0.0f, vs = 0.0f;
+        if (!CHECK || (ey < a.Ly && 2 * (j0 + ec) + ((ey + cb) & 1) < a.Lx))
+            __sincosf(q * load_as<float>(sm.other[er][Sm::HL + ec]), &vs, &vc);
+        t.cs[er][4 + ec] = vc;
+        t.sn[er][4 + ec] = vs;
+    }
+    if (tid < 4) {
+        const int hr = TYT + (tid >> 1), side = tid & 1;
+        const int hy = y0 - 1 + hr, hj = side ? j0 + kTJ : j0 - 1;
+        float hc = 0.0f, hs = 0.0f;
+        if (!CHECK || (hy < a.Ly && hj >= 0 && 2 * hj + ((hy + cb) & 1) < a.Lx))
+            __sincosf(q * load_as<float>(sm.other[hr][side ? Sm::HL + kTJ : Sm::HL - 1]), &hs, &hc);
+        t.cs[hr][side ? kTJ + 4 : 3] = hc;
+        t.sn[hr][side ? kTJ + 4 : 3] = hs;
     }
 }
 

@@ -448,8 +448,8 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
     uint4 w2 = make_uint4(0u, 0u, 0u, 0u);
     uint4 wl0 = w2, wl1 = w2;
     bool second = ROW == 1;
-    if constexpr (ROW == 2) {
-        second = ((y + c) & 1) != 0;
+    if constexpr (ROW == 2 || ROW == 0) {
+        if constexpr (ROW == 2) second = ((y + c) & 1) != 0;
         wl0 = group_call<SCHED>(a, g, h, 0u);
         wl1 = group_call<SCHED>(a, g, h, 1u);
         carry_call0(gc, wl0);
@@ -464,10 +464,7 @@ __device__ __forceinline__ void update_row(const SweepArgs& a, int y, int ly, in
         float2 op, oa;
         {
             uint4 w;
-            if constexpr (ROW == 0) {
-                w = group_call<SCHED>(a, g, h, (uint32_t)t);
-                if (t == 0) carry_call0(gc, w); else carry_call1(gc, w);
-            } else if constexpr (ROW == 2) {
+            if constexpr (ROW == 0 || ROW == 2) {
                 w = t == 0 ? wl0 : wl1;
             }
             const float2 op_f = make_float2(one_plus_uniform_f(w.x), one_plus_uniform_f(w.z));
@@ -730,7 +727,8 @@ __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* co
 
 // One tile (tile column tx, tile row ty) of colour a.colour, staged from global memory. With
 // MEASURE (black pass) the tile's sum of u_b . h_b over its existing black sites is written to
-// *eslot. Begins with a block barrier, so a block may call it for several tiles in a row.
+// *eslot. A block that runs several tiles in a row passes a block barrier between them (the
+// staging overwrites sm; the batched persistent kernel has one after every tile).
 // PDL (programmatic dependent launch, one tile per block): the block reads its own colour's values
 // and bits, then waits for the previous kernel (the other colour's pass), then lets the next
 // kernel in the stream start launching. The own colour was last written two passes back, which
@@ -774,7 +772,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous pass is complete
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
-    __syncthreads();   // the previous tile's readers are done with sm
     // ---- stage the other colour (rows y0-1 .. y0+TY, columns j0-1 .. j0+TJ). Tiles whose halo
     // lies inside the lattice (nearly all) skip the per-entry bounds checks.
     const bool interior = y0 >= 1 && y0 + TY < a.Ly && j0 >= 1 && 2 * (j0 + TJ) + 1 < a.Lx;
