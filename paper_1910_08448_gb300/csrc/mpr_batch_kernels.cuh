@@ -235,7 +235,7 @@ __device__ __forceinline__ void tile_body(const Args* __restrict__ A, int t, int
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const Prob& P = A->prob[p];
-    SweepArgs a;
+    SweepArgs a{};
     a.own = static_cast<char*>(A->ang) + (size_t)P.ang_off[colour] * sizeof(S);
     a.other = static_cast<const char*>(A->ang) + (size_t)P.ang_off[colour ^ 1] * sizeof(S);
     a.mbits = A->mb + P.mb_off[colour];

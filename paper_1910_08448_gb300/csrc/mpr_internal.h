@@ -74,6 +74,9 @@ struct SweepArgs {
                                    // prediction sites are added here (NULL: not counted)
     int nsplit;                // one-tile-per-block FP32 kernel, plain passes: the last nsplit
                                // tiles run as two half-height tiles each (0: none)
+    int late;                  // same kernel, plain passes with 16-bit spins: 1 = load each own
+                               // row just before its update (the state is resident in L2), 0 =
+                               // load all own rows before the staging
 };
 
 // TMA descriptors of one problem's half-lattices for the TMA-fed FP32 sweep kernel: per colour c

@@ -738,8 +738,11 @@ __device__ __forceinline__ void count_accepted(int n_acc, unsigned long long* co
 // PROP: bounded proposals of half-width *a.width; accepted ones counted into *a.accepted.
 // QM: 1 the caller has checked q <= 1/2 (one 2 pi wrap of the reflected angle suffices); 2 q = 1/2.
 // HM: FP16-function setting (the field's doubled angle in half2 arithmetic, atan2_doubled_h2).
+// LATE: each own row's values and bits are loaded just before the row's update instead of all
+// before the staging: fewer live registers, the better choice when the state sits in L2 (the
+// loads are short) and the worse one when they come from DRAM (the host decides).
 template <typename S, int R, bool MEASURE, int SAMPLE, bool SCHED, bool PDL = false,
-          bool PROP = false, int TJ = kTJ, int QM = 0, bool HM = false>
+          bool PROP = false, int TJ = kTJ, int QM = 0, bool HM = false, bool LATE = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, TileSmem<R, TJ>& sm,
                                            void* eslot)
 {
@@ -756,15 +759,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
     const int jb = j0 + lj;                   // first of this thread's 4 columns
 
     // ---- own rows: values and frozen bits, loaded before the staging so their latency overlaps
-    Pack4<S> mine[R];   // in the order row_of()
-    uint32_t bits[R];
+    // (LATE: at each row's update)
+    Pack4<S> mine[LATE ? 1 : R];   // in the order row_of()
+    uint32_t bits[LATE ? 1 : R];
+    if constexpr (!LATE) {
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int y = y0 + row0 + row_of<R>(i, c);
-        bits[i] = 0xFu;
-        if (y < a.Ly) {
-            load4(own + (size_t)y * a.pitch + jb, mine[i]);
-            bits[i] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
+        for (int i = 0; i < R; ++i) {
+            const int y = y0 + row0 + row_of<R>(i, c);
+            bits[i] = 0xFu;
+            if (y < a.Ly) {
+                load4(own + (size_t)y * a.pitch + jb, mine[i]);
+                bits[i] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
+            }
         }
     }
 
@@ -791,9 +797,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int tx, int ty, T
         const int y = y0 + ly;
         if (R % 2 == 0 && (i & 1) && y < a.Ly && y0 + row0 + row_of<R>(i - 1, c) >= a.Ly)
             group_carry_only<SCHED>(a, y, jb, gc);
-        if (y < a.Ly)
-            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM, TJ, HM>(i, a, y, ly, jb, lj, mine[i], bits[i],
+        if (y < a.Ly) {
+            const int k = LATE ? 0 : i;
+            if constexpr (LATE) {
+                load4(own + (size_t)y * a.pitch + jb, mine[0]);
+                bits[0] = (a.mbits[(size_t)y * a.mpitch + (jb >> 5)] >> (jb & 31)) & 0xFu;
+            }
+            update_row_i<S, R, MEASURE, SAMPLE, SCHED, PROP, QM, TJ, HM>(i, a, y, ly, jb, lj, mine[k], bits[k],
                                                              sm, e_d, e_f, pw, n_acc, gc);
+        }
     }
     if (PROP && a.accepted) count_accepted(n_acc, a.accepted);
     if (MEASURE) tile_energy(a, e_d, e_f, sm, eslot);

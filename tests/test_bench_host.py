@@ -29,6 +29,7 @@ def test_stored_counters_belong_to_their_kernel_version():
     assert got and got["bytes_per_launch"] == e["bytes_per_launch"]
     assert 0.0 < got["issue_active"] <= 1.0
     # algorithmic bytes of one 4096^2 FP16 pass: (N/2)(2(2 + p) + 1/8) = 49.7 MB; the measured
-    # DRAM bytes are below it (part of the state stays in L2) but of the same order
+    # DRAM bytes are below it (the 33.5 MB state stays in the 129 MB L2 between passes, and the
+    # capture keeps the cache as the previous pass left it) and never far above it (no re-reads)
     alg = 4096 * 4096 / 2 * (2 * 2.9 + 1 / 8)
-    assert 0.5 * alg < got["bytes_per_launch"] < 1.5 * alg
+    assert 0.1 * alg < got["bytes_per_launch"] < 1.5 * alg
