@@ -505,7 +505,7 @@ mpr_status sweeps(mpr_ctx* h, int n, double T, int flags)
     a.wait_ns = 2000000000LL;   // 2 s: a TMA copy lands in microseconds
     a.stall_test = 0;
     a.nsplit = (flags == 0) ? h->nsplit : 0;   // plain passes of the tile kernel only
-    a.late = (flags == 0) ? h->late : 0;
+    a.late = h->late;   // read by the plain-pass launches only (the red pass of a measured sweep too)
     // bounded proposals; the width adapts after every sweep that does not sample
     const bool adapt = h->prop_on && h->prop_target > 0.0 && !(flags & kSample);
     a.width = h->prop_on ? h->scal + 14 : nullptr;

@@ -632,7 +632,7 @@ def test_tma_kernel_equals_tile_kernel(mpr, orc, Lx, Ly, p, setup):
 
 @pytest.mark.parametrize("Lx,Ly,setup", [(4096, 2048, "HDS"), (2100, 1301, "SDS"), (4096, 4096, "HDS"),
                                           (2048, 1024, "SDS"), (2100, 2200, "HDS"),
-                                          (4096, 1200, "SDS")])
+                                          (4096, 1200, "SDS"), (8192, 4096, "HDS")])
 def test_tma_kernel_equals_tile_kernel_over_many_sweeps(mpr, orc, Lx, Ly, setup):
     # The two FP32 sweep kernels over 200 sweeps with several waves of tiles (and an odd Ly, whose
     # last Philox group of rows has one row): identical chains, bit for bit. On a 152-SM GPU, at
@@ -640,7 +640,9 @@ def test_tma_kernel_equals_tile_kernel_over_many_sweeps(mpr, orc, Lx, Ly, setup)
     # kernel at 2048 x 1024 all of them (one partial wave). The persistent TMA kernel (4 blocks per
     # SM with 16-bit spins, 3 with FP32) also splits at 2100 x 2200 (621 tiles, the last 13 split,
     # ragged last tile column and row) and at 4096 x 1200 (608 tiles on 456 blocks: the last 152
-    # split, the lower halves of the last tile row lie wholly below the lattice).
+    # split, the lower halves of the last tile row lie wholly below the lattice). The FP16 lattices
+    # up to 4096^2 fit the L2 and run the tile kernel's plain pass that loads each own row at its
+    # update; 8192 x 4096 (67 MB) runs the one that loads them all before the staging.
     pr = mpr_inputs.make_problem(Lx, Ly, 0.9, field_seed=43, mask_seed=44)
     _, state = _start_state(orc, pr, setup, 33)
     g0, s0, i0, _ = _kernel_run(mpr, pr, setup, state, 0, 200, 0, T=0.07)
@@ -714,10 +716,12 @@ def test_tma_wait_timeout_is_reported(mpr, orc):
 
 # --- the bench's workloads at full size, sampled --------------------------------------------
 
-@pytest.mark.parametrize("L,setup", [(4096, "HDS"), (16384, "SDS")])
+@pytest.mark.parametrize("L,setup", [(4096, "HDS"), (8192, "HDS"), (16384, "SDS")])
 def test_full_size_sweep_sampled_sites(mpr, orc, excusal_log, L, setup):
     # The workloads bench.py times (4096^2 and 16384^2, p = 0.9) through the C ABI in its launch
-    # configuration (the tile kernel, which the automatic choice keeps at these sizes): one sweep
+    # configuration (the tile kernel, which the automatic choice keeps at these sizes), and 8192^2
+    # with FP16 spins, whose 134 MB state takes the plain pass that loads all own rows before the
+    # staging (at 4096^2 the state fits the L2 and each own row is loaded at its update): one sweep
     # from an identical state; 2000 sampled sites of each colour are recomputed one by one by the
     # oracle -- red sites from the initial state, black sites from the GPU's red neighbours -- and
     # must agree within the FP32 tolerance outside near-threshold decisions. Frozen sites are
